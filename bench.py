@@ -1,0 +1,284 @@
+"""Benchmark: swept vs classic decomposition, Kuramoto-Sivashinsky, 1 GB300.
+
+Workload (one bench step = one whole solve): KS u_t = -u u_x - u_xx - u_xxxx,
+periodic, N = 2^20 FP64 points, L = 32 pi N / 128, dt = 0.005, IC
+cos(x/16)(1 + sin(x/16)) + 1e-3 U(-1, 1) (seeded), 50,000 midpoint-RK2 steps,
+swept rule with the library's default plan.  Metric: cell-updates/s
+(N * timesteps / wall time), whole job over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (plain C, OpenMP over the host cores) on
+a bounded window of the same workload; it is the reference arm of this repo.
+Under torchrun (N > 1) every rank solves its own replica (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 1 << 20
+NSTEPS = 50000
+METRIC = "cell-updates/s swept vs classic per-step GPU at 1 GB300"
+UNIT = "cell-updates/s"
+WORKLOAD = "Kuramoto-Sivashinsky N=2^20 FP64 periodic, 50,000 midpoint-RK2 steps (dt=0.005, dx=pi/4)"
+FP64_FLOPS_PER_SUBSTEP = 18  # 7 fma (2 flops) + 2 add + 2 mul per point per sub-timestep
+FP64_INSTR_PER_SUBSTEP = 11
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(n, seconds, threads):
+    """Oracle cell-updates/s on a bounded window of the workload (grid N, few steps)."""
+    import oracle
+    from paper_1612_02495_gb300 import inputs
+
+    p = inputs.ks_problem(n=n)
+    t0 = time.perf_counter()
+    oracle.ks(p["u0"], p["dx"], p["dt"], p["nu"], 2, threads=threads)
+    per_step = max(time.perf_counter() - t0, 1e-6) / 2
+    steps = int(max(2, min(100000, seconds / per_step)))
+    t0 = time.perf_counter()
+    oracle.ks(p["u0"], p["dx"], p["dt"], p["nu"], steps, threads=threads)
+    dt = time.perf_counter() - t0
+    return n * steps / dt, steps, dt
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    threads = os.cpu_count() or 1
+    oracle.build.build()
+    rates = []
+    steps_used = 0
+    for i in range(args.warmup + args.steps):
+        r, st, _ = cpu_oracle_rate(N, 8.0, threads)
+        if i >= args.warmup:
+            rates.append(r)
+            steps_used = st
+    v = float(np.mean(rates))
+    ms = N * NSTEPS / v * 1e3
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n": N, "nsteps": NSTEPS, "oracle_window_steps": steps_used},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                            "sample": "oracle (plain C, OpenMP over %d threads) on the full N=2^20 grid for a %d-step "
+                                      "window per bench step; ms_per_step extrapolates to 50,000 steps"
+                                      % (threads, steps_used)},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-classic", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    __graft_entry__.build() if rank == 0 else None
+    if ws > 1:
+        dist.barrier()
+    from paper_1612_02495_gb300 import inputs
+    from paper_1612_02495_gb300 import swept as S
+
+    p = inputs.ks_problem(n=N, seed=1 + rank)
+    sol = S.Solver(S.KS, S.F64, N, p["dx"], p["dt"], p["nu"])
+    plan = sol.plan
+    stream = torch.cuda.current_stream()
+    u0 = torch.from_numpy(p["u0"]).cuda()
+    u = u0.clone()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    launches_per_step = (2 * NSTEPS) // plan["half_cycle"] + 1 + (2 if (2 * NSTEPS) % plan["half_cycle"] else 0)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, k, w):
+        for _ in range(w):
+            u.copy_(u0)
+            fn(u)
+        barrier()
+        total = 0.0
+        evs = []
+        for _ in range(k):
+            u.copy_(u0)
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn(u)
+            b.record(stream)
+            evs.append((a, b))
+        barrier()
+        for a, b in evs:
+            total += a.elapsed_time(b)
+        ms = total / k
+        if ws > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    clocks = Clocks(local)
+    clocks.start()
+    ms = timed(lambda x: sol.step(x, NSTEPS), args.steps, args.warmup)
+    clk = clocks.stop()
+    sol.sync_status()
+    value = ws * N * NSTEPS / (ms * 1e-3)
+
+    ms_classic = None
+    if not args.no_classic:
+        ms_classic = timed(lambda x: sol.classic(x, NSTEPS), max(1, args.steps // 2), 1)
+
+    # end to end through the C ABI with host buffers (pinned): H2D + solve + D2H per step
+    h_in = torch.from_numpy(p["u0"]).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    sol.run_host(h_in, h_out, u, NSTEPS)
+    barrier()
+    e2e_ms = []
+    for _ in range(max(1, args.steps // 2)):
+        t0 = time.perf_counter()
+        sol.run_host(h_in, h_out, u, NSTEPS)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e = float(np.mean(e2e_ms))
+    if ws > 1:
+        t = torch.tensor([e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = float(t.item())
+
+    # dominant kernel: the diamond pass, timed with CUDA events on the launching stream
+    u.copy_(u0)
+    prof = sol.profile_passes(u, NSTEPS)
+    d_ms, d_n = prof["diamond"]
+    d_avg = d_ms / max(d_n, 1)
+    flops_per_diamond = FP64_FLOPS_PER_SUBSTEP * N * plan["half_cycle"]
+    pk = peaks()
+    fp64_peak_tflops = 1.2  # measured DFMA rate 0.60 T/s x 2 flops (FP64 pipe, GB300)
+    achieved = flops_per_diamond / (d_avg * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak_tflops, "traffic": None, "kernel": "k_swept_diamond<double, KsOp>",
+                "peak_source": "measured FP64 FMA issue rate on this GB300 (0.60e12 DFMA/s), x2 flops",
+                "pipe_frac": (FP64_INSTR_PER_SUBSTEP * N * plan["half_cycle"] / (d_avg * 1e-3)) / 0.60e12,
+                "diamond_ms_avg": d_avg, "diamond_share": d_ms / max(sum(v[0] for v in prof.values()), 1e-9)}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n": N, "nsteps": NSTEPS, "tile_w": plan["tile_w"],
+                      "threads": plan["threads"], "half_cycle": plan["half_cycle"],
+                      "l2": "flushed (256 MB write) before every timed step", "parallelism": "replicas"},
+           "gpu_launches": launches_per_step * args.steps,
+           "e2e": {"value": ws * N * NSTEPS / (e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": N * 8,
+                   "d2h_bytes_per_step": N * 8},
+           "roofline": roofline, "clocks": clk}
+    if ms_classic:
+        out["classic"] = {"value": ws * N * NSTEPS / (ms_classic * 1e-3), "ms_per_step": ms_classic}
+        out["speedup_vs_classic"] = ms_classic / ms
+    if rank == 0 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        r, st, secs = cpu_oracle_rate(N, 10.0, threads)
+        out["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": "oracle on the full N=2^20 grid for %d steps (%.1f s, OpenMP %d threads)"
+                                         % (st, secs, threads)}
+    if rank == 0:
+        print(json.dumps(out))
+    sol.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

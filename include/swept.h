@@ -1,0 +1,187 @@
+/*
+ * swept.h - C ABI of the GB300 swept time-space decomposition library (libswept.so).
+ *
+ * Method: Magee & Niemeyer, "An initial investigation of the performance of
+ * GPU-based swept time-space decomposition" (arXiv:1612.02495).
+ *   - Problem statement: an explicit 1D stencil scheme on n grid points with a
+ *     boundary condition, advanced a number of timesteps (Section "Test cases",
+ *     Eq. HeatDisc, Eq. KSDisc, Appendix).
+ *   - Swept rule: each thread block keeps a tile ("node") in shared memory,
+ *     advances it as a shrinking triangle, passes only the triangle edges, then
+ *     completes diamonds, zig-zagging the tiles by half a tile each pass
+ *     (Section "First-order", Figs. firstorder and collection; Section
+ *     "Second-order extended stencil", Fig. secondordersolution).
+ *   - Classic decomposition: one kernel per sub-timestep through global memory
+ *     (Section "Classic scheme", Fig. ClassicCode).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named *_dev are CUDA device pointers owned by the caller; the
+ *     library never allocates device memory (no cudaMalloc) and never frees
+ *     caller memory.  Pointers named *_host are host pointers owned by the caller.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls that take a stream are asynchronous on it unless stated otherwise.
+ *   - Every call returns a swept_status and never throws.  On failure the
+ *     handle (if any) keeps a message readable with swept_last_error().
+ *   - Device-side errors (a bounded wait that ran out, a failed consistency
+ *     check inside a kernel) are latched in a word of the bound workspace and
+ *     returned by swept_sync_status().
+ *   - A handle is not thread-safe: calls on one handle must not overlap.
+ *
+ * State layout in device memory (dtype fixed per handle, contiguous):
+ *   SWEPT_HEAT, SWEPT_KS : n values u[0..n)
+ *   SWEPT_EULER          : 3*n values, structure of arrays (rho[0..n) | m[0..n) | E[0..n))
+ */
+#ifndef SWEPT_H
+#define SWEPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SWEPT_OK = 0,
+  SWEPT_EINVAL = 1,            /* bad argument or configuration */
+  SWEPT_ENOMEM_WORKSPACE = 2,  /* bound workspace smaller than swept_workspace_size() */
+  SWEPT_ECUDA = 3,             /* a CUDA runtime call failed (message in swept_last_error) */
+  SWEPT_ETIMEOUT = 4,          /* a bounded device-side wait ran out */
+  SWEPT_EUNSUPPORTED = 5,      /* valid request this build does not implement */
+  SWEPT_ENOWORKSPACE = 6,      /* no workspace bound yet */
+  SWEPT_EDEVICE = 7            /* a kernel's own consistency check failed */
+} swept_status;
+
+typedef enum {
+  SWEPT_HEAT = 0,  /* u_t = alpha u_xx, FTCS (Eq. HeatDisc): r=1, one stage */
+  SWEPT_KS = 1,    /* u_t = -u u_x - u_xx - nu u_xxxx, Eq. KSDisc + midpoint RK2 (Appendix): r=2, two stages */
+  SWEPT_EULER = 2  /* 1D Euler, MUSCL-minmod + Rusanov + SSP-RK2 (not in the paper): r=2, two stages */
+} swept_scheme;
+
+typedef enum { SWEPT_F32 = 0, SWEPT_F64 = 1 } swept_dtype;
+
+typedef enum {
+  SWEPT_BC_PERIODIC = 0,   /* index i+k taken mod n (Appendix) */
+  SWEPT_BC_REFLECTIVE = 1  /* mirror walls at x = -1/2 and n - 1/2: insulated ends for heat,
+                              reflective walls (momentum negated) for Euler; not for KS */
+} swept_bc;
+
+/*
+ * Problem and launch configuration.
+ *   n        grid points (>= 2 * tile_w, and a multiple of tile_w)
+ *   dx, dt   grid spacing and timestep
+ *   param[0] heat: alpha (diffusivity); KS: nu (factor on u_xxxx, 1 = the
+ *            paper's equation); Euler: gamma
+ *   tile_w   points per tile W (the paper's node size / threads per block);
+ *            0 = chosen by the library.  Must be a multiple of 4*r (r = 1 heat,
+ *            2 KS/Euler), so that the half-cycle h = W/(2r) is even.
+ *   threads  threads per block, 0 = chosen by the library (<= 1024, multiple of 32)
+ * Stability (Fo <= 1/2, CFL) is the caller's responsibility and is not checked.
+ */
+typedef struct {
+  int32_t scheme;   /* swept_scheme */
+  int32_t dtype;    /* swept_dtype */
+  int32_t bc;       /* swept_bc */
+  int32_t reserved0;
+  int64_t n;
+  double dx;
+  double dt;
+  double param[4];
+  int32_t tile_w;
+  int32_t threads;
+  int32_t reserved[6];
+} swept_config;
+
+/* Plan chosen by swept_init (read-only report). */
+typedef struct {
+  int32_t tile_w;          /* W */
+  int32_t threads;         /* threads per block */
+  int32_t half_cycle;      /* h = W / (2r): sub-timesteps advanced per swept pass */
+  int32_t radius;          /* r: stencil radius of one sub-timestep */
+  int32_t stages;          /* S: sub-timesteps per timestep */
+  int32_t components;      /* C: values per grid point */
+  int64_t tiles;           /* n / W */
+  int64_t smem_bytes;      /* dynamic shared memory per block of the swept kernels */
+  int64_t workspace_bytes; /* same as swept_workspace_size() */
+} swept_plan_info;
+
+typedef struct swept_handle swept_handle;
+
+/* Validate `cfg`, choose the plan and create a handle (host memory only).
+ * Errors: SWEPT_EINVAL (bad cfg, NULL pointers), SWEPT_ECUDA (no device). */
+swept_status swept_init(const swept_config* cfg, swept_handle** out);
+
+/* Bytes of device workspace the handle needs: the ping-pong edge buffers of
+ * the swept passes (Section "First-order": the global "left"/"right" arrays),
+ * the classic path's intermediate stage array, and a status word. */
+swept_status swept_workspace_size(const swept_handle* h, size_t* bytes);
+
+/* Bind caller-owned device workspace (>= swept_workspace_size bytes, 256-byte
+ * aligned).  Rebinding drops cached CUDA graphs.  Errors: SWEPT_EINVAL,
+ * SWEPT_ENOMEM_WORKSPACE. */
+swept_status swept_bind_workspace(swept_handle* h, void* ws_dev, size_t bytes);
+
+/* Advance u_dev (layout above) by nsteps full timesteps in place with the swept
+ * rule: up-triangle, diamonds, down-triangle, then a trapezoid pair for the
+ * sub-timesteps left over (nsteps * S mod h).  nsteps == 0 is a no-op.
+ * Results equal classic_step_n bit for bit (same per-point operation order).
+ * Errors: SWEPT_EINVAL, SWEPT_ENOWORKSPACE, SWEPT_ECUDA. */
+swept_status swept_step_n(swept_handle* h, void* u_dev, int64_t nsteps, void* stream);
+
+/* Same advance with the classic decomposition: one kernel per sub-timestep
+ * (Fig. ClassicCode), captured into CUDA graphs. */
+swept_status classic_step_n(swept_handle* h, void* u_dev, int64_t nsteps, void* stream);
+
+/* End-to-end call for callers holding host data: copies u_host_in (layout
+ * above) to u_dev, advances nsteps (swept if use_swept != 0, else classic),
+ * copies the result to u_host_out, and synchronizes `stream` before returning.
+ * u_host_in may equal u_host_out.  Pinned host memory gives asynchronous copies. */
+swept_status swept_run_host(swept_handle* h, const void* u_host_in, void* u_host_out, void* u_dev, int64_t nsteps,
+                            int32_t use_swept, void* stream);
+
+/* Discrete adjoint of swept_step_n for SWEPT_KS and SWEPT_HEAT in SWEPT_F64.
+ * Given u0_dev (the initial state) and gT_dev = dL/du(T) after nsteps steps,
+ * writes g_u0_dev = dL/du0 and g_param_dev[0] = dL/dparam[0] (nu or alpha).
+ * The forward states are recomputed from checkpoints stored in ckpt_dev
+ * (size from swept_adjoint_ckpt_size).  Not in the paper.
+ * Errors: SWEPT_EUNSUPPORTED (scheme/dtype), SWEPT_EINVAL, SWEPT_ENOMEM_WORKSPACE. */
+swept_status swept_adjoint_ckpt_size(const swept_handle* h, int64_t nsteps, size_t* bytes);
+swept_status swept_adjoint(swept_handle* h, const void* u0_dev, const void* gT_dev, int64_t nsteps, void* g_u0_dev,
+                           void* g_param_dev, void* ckpt_dev, size_t ckpt_bytes, void* stream);
+
+/* Tracing: run swept_step_n's launch sequence for nsteps on `stream` with
+ * direct launches (no graph) and a CUDA event pair around every launch, then
+ * synchronize.  out_ms[4] receives the summed device time and out_count[4] the
+ * number of launches of each kind: [0] up-triangle, [1] diamond, [2]
+ * down-triangle, [3] remainder pair.  u_dev is advanced exactly as by
+ * swept_step_n. */
+swept_status swept_profile_passes(swept_handle* h, void* u_dev, int64_t nsteps, void* stream, double* out_ms,
+                                  int64_t* out_count);
+
+/* Plan report. */
+swept_status swept_get_plan(const swept_handle* h, swept_plan_info* out);
+
+/* Synchronize `stream`, then read and clear the device-side error word.
+ * Returns SWEPT_OK, SWEPT_ETIMEOUT or SWEPT_EDEVICE. */
+swept_status swept_sync_status(swept_handle* h, void* stream);
+
+/* Host-only check of the swept schedule (no GPU work): replays the index
+ * arithmetic the kernels use for nsteps full timesteps on symbolic
+ * (point, sub-timestep) tags and verifies that every point of every
+ * sub-timestep is computed exactly once, only after all of its stencil inputs,
+ * and that the final tier is complete.  computed_out (may be NULL) receives the
+ * number of point updates performed.  Returns SWEPT_OK or SWEPT_EDEVICE with a
+ * message in swept_last_error. */
+swept_status swept_check_schedule(swept_handle* h, int64_t nsteps, int64_t* computed_out);
+
+/* Copy the last error message (NUL-terminated, truncated to len). */
+swept_status swept_last_error(const swept_handle* h, char* buf, size_t len);
+
+/* Destroy the handle and its cached graphs; NULL is a no-op. */
+void swept_free(swept_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWEPT_H */

@@ -1,0 +1,440 @@
+// C-ABI runtime: plan selection, workspace layout, launch sequencing of the
+// swept and classic paths, and CUDA-graph caching (include/swept.h).
+#include <stdio.h>
+#include <string.h>
+
+#include <functional>
+#include <new>
+#include <string>
+
+#include "runtime.h"
+#include "swept_phases.cuh"
+
+using swept::Geom;
+using swept::SchemeImpl;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kGb300Sms = 152;
+constexpr int kGb300SmemOptin = 232448;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+swept_status fail(swept_handle* h, swept_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  return st;
+}
+swept_status cuda_fail(swept_handle* h, cudaError_t e, const char* where) {
+  return fail(h, SWEPT_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+const SchemeImpl* pick_impl(int scheme, int dtype) {
+  if (dtype != SWEPT_F32 && dtype != SWEPT_F64) return nullptr;
+  switch (scheme) {
+    case SWEPT_HEAT: return swept::heat_impl(dtype);
+    case SWEPT_KS: return swept::ks_impl(dtype);
+    case SWEPT_EULER: return swept::euler_impl(dtype);
+    default: return nullptr;
+  }
+}
+
+bool tile_ok(int64_t n, int W, int R) { return W >= 4 * R && W % (4 * R) == 0 && n % W == 0 && n / W >= 2; }
+
+// Default tile width: the largest W <= 1024 (multiple of 4R, dividing n) that
+// still gives at least two blocks per SM; else at least one per SM; else the
+// smallest legal W.
+int choose_tile(int64_t n, int R, int sms) {
+  int best = 0;
+  for (int W = 4 * R; W <= 1024; W += 4 * R)
+    if (tile_ok(n, W, R) && n / W >= 2 * sms) best = W;
+  if (best) return best;
+  for (int W = 4 * R; W <= 1024; W += 4 * R)
+    if (tile_ok(n, W, R) && n / W >= sms) best = W;
+  if (best) return best;
+  for (int W = 4 * R; W <= 4096; W += 4 * R)
+    if (tile_ok(n, W, R)) return W;
+  return 0;
+}
+
+std::string key_of(const char* kind, const void* u, int64_t a, int64_t b = 0) {
+  char buf[128];
+  snprintf(buf, sizeof buf, "%s:%p:%lld:%lld", kind, u, (long long)a, (long long)b);
+  return buf;
+}
+
+// Launch a cached graph for `key`, capturing `issue` on the private stream the
+// first time.  If the caller's stream is itself being captured, issue directly.
+swept_status run_graph(swept_handle* h, const std::string& key, cudaStream_t user,
+                       const std::function<cudaError_t(cudaStream_t)>& issue) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(user, &cs);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamIsCapturing");
+  if (cs != cudaStreamCaptureStatusNone) {
+    e = issue(user);
+    return e == cudaSuccess ? SWEPT_OK : cuda_fail(h, e, "kernel launch");
+  }
+  auto it = h->graphs.find(key);
+  if (it == h->graphs.end()) {
+    e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamBeginCapture");
+    cudaError_t le = issue(h->cap);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->cap, &graph);
+    if (le != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(h, le, "kernel launch during capture");
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    it = h->graphs.emplace(key, exec).first;
+  }
+  e = cudaGraphLaunch(it->second, user);
+  return e == cudaSuccess ? SWEPT_OK : cuda_fail(h, e, "cudaGraphLaunch");
+}
+
+void drop_graphs(swept_handle* h) {
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+}
+
+// First GPU use of a handle: the private capture stream and the shared-memory
+// limit of the swept kernels.  Later calls check the current device matches.
+swept_status ensure_device(swept_handle* h) {
+  if (h->device < 0) return fail(h, SWEPT_ECUDA, "no CUDA device was available when the handle was created");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaGetDevice");
+  if (dev != h->device) return fail(h, SWEPT_EINVAL, "current device differs from the handle's device");
+  if (!h->cap) {
+    if (h->smem > 48 * 1024) {
+      e = h->impl->prepare(h->smem);
+      if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)");
+    }
+    e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamCreateWithFlags");
+  }
+  return SWEPT_OK;
+}
+
+swept_status check_ready(swept_handle* h, void* u_dev, int64_t nsteps) {
+  if (!h) return SWEPT_EINVAL;
+  if (!u_dev || nsteps < 0) return fail(h, SWEPT_EINVAL, "u_dev is NULL or nsteps < 0");
+  if (!h->ws) return fail(h, SWEPT_ENOWORKSPACE, "no workspace bound (swept_bind_workspace)");
+  if (h->ws_bound < h->ws_bytes) return fail(h, SWEPT_ENOMEM_WORKSPACE, "bound workspace too small");
+  return ensure_device(h);
+}
+
+// ---------------------------------------------------------------------------
+// swept launch sequence: launch index i in [from, to) of for_each_launch
+// ---------------------------------------------------------------------------
+cudaError_t issue_swept(swept_handle* h, void* u, int64_t n_sub, int64_t from, int64_t to, cudaStream_t s) {
+  const Geom& g = h->g;
+  const SchemeImpl* im = h->impl;
+  void* eb[2] = {h->ws + h->off_e0, h->ws + h->off_e1};
+  int64_t idx = 0;
+  cudaError_t err = cudaSuccess;
+  swept::for_each_launch(g, n_sub, [&](int kind, int odd, int mode, int hh, int64_t pass) {
+    const int64_t i = idx++;
+    if (i < from || i >= to || err != cudaSuccess) return;
+    if (kind == 0) {
+      const int out = pass >= 0 ? (int)(pass & 1) : 0;
+      err = im->up(g, h->k, u, u, eb[out], hh, mode == swept::MODE_GAP, h->threads, h->smem, s);
+    } else {
+      const int in = pass >= 1 ? (int)((pass - 1) & 1) : 0;
+      const int out = pass >= 1 ? (int)(pass & 1) : 1;
+      err = im->diamond(g, h->k, u, eb[in], eb[out], odd, mode, hh, h->threads, h->smem, s);
+    }
+  });
+  return err;
+}
+
+int64_t swept_launch_count(const Geom& g, int64_t n_sub) {
+  const int64_t q = n_sub / g.h, rem = n_sub % g.h;
+  return (q > 0 ? q + 1 : 0) + (rem > 0 ? 2 : 0);
+}
+
+// classic sub-timesteps [k0, k1) of a run; for a one-stage scheme the state
+// ping-pongs between u (even k) and tmp (odd k)
+cudaError_t issue_classic(swept_handle* h, void* u, int64_t k0, int64_t k1, cudaStream_t s) {
+  const Geom& g = h->g;
+  void* tmp = h->ws + h->off_tmp;
+  for (int64_t k = k0; k < k1; ++k) {
+    cudaError_t e;
+    if (g.S == 1) {
+      const bool even = (k & 1) == 0;
+      e = h->impl->classic(g, h->k, 0, even ? u : tmp, even ? tmp : u, s);
+    } else {
+      const int stage = (int)(k % g.S);
+      e = stage == 0 ? h->impl->classic(g, h->k, 0, u, tmp, s) : h->impl->classic(g, h->k, 1, tmp, u, s);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+swept_status swept_init(const swept_config* cfg, swept_handle** out) {
+  if (!cfg || !out) return SWEPT_EINVAL;
+  *out = nullptr;
+  const SchemeImpl* im = pick_impl(cfg->scheme, cfg->dtype);
+  if (!im) return SWEPT_EINVAL;
+  if (cfg->bc != SWEPT_BC_PERIODIC && cfg->bc != SWEPT_BC_REFLECTIVE) return SWEPT_EINVAL;
+  if (cfg->scheme == SWEPT_KS && cfg->bc != SWEPT_BC_PERIODIC) return SWEPT_EINVAL;
+  if (!(cfg->dx > 0) || !(cfg->dt > 0) || cfg->n < 8) return SWEPT_EINVAL;
+  if (cfg->scheme == SWEPT_EULER && !(cfg->param[0] > 1.0)) return SWEPT_EINVAL;
+  swept_handle* h = new (std::nothrow) swept_handle();
+  if (!h) return SWEPT_EINVAL;
+  h->cfg = *cfg;
+  h->impl = im;
+  // Plan from the current device's properties; without a usable device the
+  // plan uses GB300's (152 SMs, 227 KB opt-in shared memory) so that the host
+  // schedule check still works, and every compute call fails with SWEPT_ECUDA.
+  int max_smem = kGb300SmemOptin;
+  h->sm_count = kGb300Sms;
+  h->device = -1;
+  int dev = -1;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    int sms = 0, sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess) {
+      h->device = dev;
+      h->sm_count = sms;
+      max_smem = sm;
+    }
+  }
+  cudaGetLastError();  // clear a no-device error
+  cudaError_t e = cudaSuccess;
+  const int R = im->R;
+  int W = cfg->tile_w > 0 ? cfg->tile_w : choose_tile(cfg->n, R, h->sm_count);
+  if (W <= 0 || !tile_ok(cfg->n, W, R)) {
+    delete h;
+    return SWEPT_EINVAL;
+  }
+  Geom& g = h->g;
+  g.N = cfg->n;
+  g.W = W;
+  g.R = R;
+  g.S = im->S;
+  g.C = im->C;
+  g.h = W / (2 * R);
+  g.M = W + 2 * R;
+  g.nt = cfg->n / W;
+  g.E = 2 * g.h * g.C * 2 * R;
+  g.bc = cfg->bc;
+  int th = cfg->threads > 0 ? cfg->threads : (W >= 256 ? 256 : ((W + 31) / 32) * 32);
+  if (th < 32 || th > 1024 || th % 32 != 0) {
+    delete h;
+    return SWEPT_EINVAL;
+  }
+  h->threads = th;
+  h->smem = (size_t)im->smem_values(g.M) * im->value_bytes;
+  if (h->smem > (size_t)max_smem) {
+    delete h;
+    return SWEPT_EINVAL;
+  }
+  im->make_consts(cfg->param, cfg->dx, cfg->dt, h->k);
+  const size_t vb = (size_t)im->value_bytes;
+  const size_t ebytes = align_up((size_t)g.nt * g.E * vb);
+  h->off_e0 = 0;
+  h->off_e1 = ebytes;
+  h->off_tmp = 2 * ebytes;
+  h->off_status = h->off_tmp + align_up((size_t)g.N * g.C * vb);
+  h->ws_bytes = h->off_status + kAlign;
+  (void)e;
+  *out = h;
+  return SWEPT_OK;
+}
+
+swept_status swept_workspace_size(const swept_handle* h, size_t* bytes) {
+  if (!h || !bytes) return SWEPT_EINVAL;
+  *bytes = h->ws_bytes;
+  return SWEPT_OK;
+}
+
+swept_status swept_bind_workspace(swept_handle* h, void* ws_dev, size_t bytes) {
+  if (!h) return SWEPT_EINVAL;
+  if (!ws_dev || ((uintptr_t)ws_dev % kAlign) != 0) return fail(h, SWEPT_EINVAL, "workspace NULL or not 256-byte aligned");
+  if (bytes < h->ws_bytes) return fail(h, SWEPT_ENOMEM_WORKSPACE, "workspace smaller than swept_workspace_size()");
+  swept_status st = ensure_device(h);
+  if (st != SWEPT_OK) return st;
+  drop_graphs(h);
+  h->ws = (char*)ws_dev;
+  h->ws_bound = bytes;
+  cudaError_t e = cudaMemset(h->ws + h->off_status, 0, kAlign);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemset(status)");
+  return SWEPT_OK;
+}
+
+swept_status swept_step_n(swept_handle* h, void* u_dev, int64_t nsteps, void* stream) {
+  swept_status st = check_ready(h, u_dev, nsteps);
+  if (st != SWEPT_OK || nsteps == 0) return st;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n_sub = nsteps * h->g.S;
+  const int64_t L = swept_launch_count(h->g, n_sub);
+  const int64_t kChunk = 512;  // diamond passes per cached body graph
+  if (L <= 2 * kChunk + 4) {
+    return run_graph(h, key_of("swept", u_dev, nsteps), s,
+                     [&](cudaStream_t cs) { return issue_swept(h, u_dev, n_sub, 0, L, cs); });
+  }
+  // head (up-triangle), a reusable body of kChunk diamonds (even count, so
+  // pass parities and edge buffers repeat), then the tail
+  const int64_t q = n_sub / h->g.h;
+  const int64_t reps = (q - 1) / kChunk;
+  st = run_graph(h, key_of("swept_head", u_dev, 0), s,
+                 [&](cudaStream_t cs) { return issue_swept(h, u_dev, n_sub, 0, 1, cs); });
+  if (st != SWEPT_OK) return st;
+  for (int64_t r = 0; r < reps; ++r) {
+    st = run_graph(h, key_of("swept_body", nullptr, kChunk), s,
+                   [&](cudaStream_t cs) { return issue_swept(h, u_dev, n_sub, 1, 1 + kChunk, cs); });
+    if (st != SWEPT_OK) return st;
+  }
+  const int64_t t0 = 1 + reps * kChunk;
+  return run_graph(h, key_of("swept_tail", u_dev, nsteps), s,
+                   [&](cudaStream_t cs) { return issue_swept(h, u_dev, n_sub, t0, L, cs); });
+}
+
+swept_status classic_step_n(swept_handle* h, void* u_dev, int64_t nsteps, void* stream) {
+  swept_status st = check_ready(h, u_dev, nsteps);
+  if (st != SWEPT_OK || nsteps == 0) return st;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const int64_t S = h->g.S;
+  const int64_t n_sub = nsteps * S;
+  const int64_t kBody = 512;  // full steps per cached body graph (even: heat returns to u)
+  const int64_t reps = nsteps / kBody;
+  for (int64_t r = 0; r < reps; ++r) {
+    st = run_graph(h, key_of("classic_body", u_dev, kBody), s,
+                   [&](cudaStream_t cs) { return issue_classic(h, u_dev, 0, kBody * S, cs); });
+    if (st != SWEPT_OK) return st;
+  }
+  const int64_t k0 = reps * kBody * S;
+  if (k0 == n_sub) return SWEPT_OK;
+  return run_graph(h, key_of("classic_tail", u_dev, nsteps - reps * kBody), s, [&](cudaStream_t cs) {
+    cudaError_t e = issue_classic(h, u_dev, k0, n_sub, cs);
+    if (e == cudaSuccess && S == 1 && (n_sub & 1))
+      e = h->impl->copy(h->g.N * h->g.C, h->ws + h->off_tmp, u_dev, cs);
+    return e;
+  });
+}
+
+swept_status swept_run_host(swept_handle* h, const void* u_host_in, void* u_host_out, void* u_dev, int64_t nsteps,
+                            int32_t use_swept, void* stream) {
+  if (!h) return SWEPT_EINVAL;
+  if (!u_host_in || !u_host_out) return fail(h, SWEPT_EINVAL, "host buffer is NULL");
+  swept_status st = check_ready(h, u_dev, nsteps);
+  if (st != SWEPT_OK) return st;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)h->g.N * h->g.C * h->impl->value_bytes;
+  cudaError_t e = cudaMemcpyAsync(u_dev, u_host_in, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync H2D");
+  st = use_swept ? swept_step_n(h, u_dev, nsteps, stream) : classic_step_n(h, u_dev, nsteps, stream);
+  if (st != SWEPT_OK) return st;
+  e = cudaMemcpyAsync(u_host_out, u_dev, bytes, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpyAsync D2H");
+  e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? SWEPT_OK : cuda_fail(h, e, "cudaStreamSynchronize");
+}
+
+swept_status swept_adjoint_ckpt_size(const swept_handle* h, int64_t nsteps, size_t* bytes) {
+  (void)h; (void)nsteps; (void)bytes;
+  return SWEPT_EUNSUPPORTED;
+}
+
+swept_status swept_adjoint(swept_handle* h, const void* u0_dev, const void* gT_dev, int64_t nsteps, void* g_u0_dev,
+                           void* g_param_dev, void* ckpt_dev, size_t ckpt_bytes, void* stream) {
+  (void)u0_dev; (void)gT_dev; (void)nsteps; (void)g_u0_dev; (void)g_param_dev; (void)ckpt_dev; (void)ckpt_bytes;
+  (void)stream;
+  return fail(h, SWEPT_EUNSUPPORTED, "adjoint not available in this build");
+}
+
+swept_status swept_profile_passes(swept_handle* h, void* u_dev, int64_t nsteps, void* stream, double* out_ms,
+                                  int64_t* out_count) {
+  swept_status st = check_ready(h, u_dev, nsteps);
+  if (st != SWEPT_OK) return st;
+  if (!out_ms || !out_count) return fail(h, SWEPT_EINVAL, "NULL output arrays");
+  for (int i = 0; i < 4; ++i) {
+    out_ms[i] = 0.0;
+    out_count[i] = 0;
+  }
+  const cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n_sub = nsteps * h->g.S;
+  const int64_t L = swept_launch_count(h->g, n_sub);
+  std::vector<cudaEvent_t> ev((size_t)(2 * L), nullptr);
+  std::vector<int> kind((size_t)L, 0);
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; i < ev.size() && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+  int64_t idx = 0;
+  if (e == cudaSuccess) {
+    swept::for_each_launch(h->g, n_sub, [&](int k, int, int mode, int, int64_t pass) {
+      kind[(size_t)idx] = pass < 0 ? 3 : (k == 0 ? 0 : (mode == swept::MODE_DOWN ? 2 : 1));
+      ++idx;
+    });
+    for (int64_t i = 0; i < L && e == cudaSuccess; ++i) {
+      e = cudaEventRecord(ev[(size_t)(2 * i)], s);
+      if (e == cudaSuccess) e = issue_swept(h, u_dev, n_sub, i, i + 1, s);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[(size_t)(2 * i + 1)], s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int64_t i = 0; i < L && e == cudaSuccess; ++i) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, ev[(size_t)(2 * i)], ev[(size_t)(2 * i + 1)]);
+      out_ms[kind[(size_t)i]] += ms;
+      out_count[kind[(size_t)i]] += 1;
+    }
+  }
+  for (auto x : ev)
+    if (x) cudaEventDestroy(x);
+  return e == cudaSuccess ? SWEPT_OK : cuda_fail(h, e, "swept_profile_passes");
+}
+
+swept_status swept_get_plan(const swept_handle* h, swept_plan_info* out) {
+  if (!h || !out) return SWEPT_EINVAL;
+  out->tile_w = h->g.W;
+  out->threads = h->threads;
+  out->half_cycle = h->g.h;
+  out->radius = h->g.R;
+  out->stages = h->g.S;
+  out->components = h->g.C;
+  out->tiles = h->g.nt;
+  out->smem_bytes = (int64_t)h->smem;
+  out->workspace_bytes = (int64_t)h->ws_bytes;
+  return SWEPT_OK;
+}
+
+swept_status swept_sync_status(swept_handle* h, void* stream) {
+  if (!h) return SWEPT_EINVAL;
+  if (!h->ws) return fail(h, SWEPT_ENOWORKSPACE, "no workspace bound");
+  const cudaStream_t s = (cudaStream_t)stream;
+  int32_t word = 0;
+  cudaError_t e = cudaMemcpyAsync(&word, h->ws + h->off_status, sizeof word, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->off_status, 0, sizeof word, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "swept_sync_status");
+  if (word == 0) return SWEPT_OK;
+  return fail(h, word == SWEPT_ETIMEOUT ? SWEPT_ETIMEOUT : SWEPT_EDEVICE, "device-side error word set");
+}
+
+swept_status swept_check_schedule(swept_handle* h, int64_t nsteps, int64_t* computed_out) {
+  if (!h || nsteps < 0) return SWEPT_EINVAL;
+  return swept::check_schedule(h, nsteps, computed_out);
+}
+
+swept_status swept_last_error(const swept_handle* h, char* buf, size_t len) {
+  if (!h || !buf || len == 0) return SWEPT_EINVAL;
+  snprintf(buf, len, "%s", h->err.c_str());
+  return SWEPT_OK;
+}
+
+void swept_free(swept_handle* h) {
+  if (!h) return;
+  drop_graphs(h);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  delete h;
+}
+
+}  // extern "C"

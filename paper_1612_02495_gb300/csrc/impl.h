@@ -1,0 +1,36 @@
+// Per-(scheme, dtype) launch table, filled by one translation unit per scheme
+// (impl_heat.cu, impl_ks.cu, impl_euler.cu) and used by the runtime (api.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "swept_geom.cuh"
+
+
+namespace swept {
+
+constexpr int KBYTES = 64;  // room for any scheme's constant struct
+
+struct SchemeImpl {
+  int R, S, C;
+  int value_bytes;
+  // constants of the scheme for this config, written into kbuf (<= KBYTES)
+  void (*make_consts)(const double* param, double dx, double dt, void* kbuf);
+  int64_t (*smem_values)(int M);
+  // raise the dynamic shared-memory limit of the swept kernels to `bytes`
+  cudaError_t (*prepare)(size_t bytes);
+  cudaError_t (*up)(const Geom& g, const void* k, const void* u_in, void* u_out, void* e_out, int hh, int write_top,
+                    int threads, size_t smem, cudaStream_t s);
+  cudaError_t (*diamond)(const Geom& g, const void* k, void* u_out, const void* e_in, void* e_out, int odd, int mode,
+                         int hh, int threads, size_t smem, cudaStream_t s);
+  // one classic sub-timestep (stage 0 or 1) from `in` into `out`
+  cudaError_t (*classic)(const Geom& g, const void* k, int stage, const void* in, void* out, cudaStream_t s);
+  cudaError_t (*copy)(int64_t n, const void* src, void* dst, cudaStream_t s);
+};
+
+const SchemeImpl* heat_impl(int dtype);
+const SchemeImpl* ks_impl(int dtype);
+const SchemeImpl* euler_impl(int dtype);
+
+}  // namespace swept

@@ -1,0 +1,50 @@
+// Launch wrappers shared by the per-scheme translation units.
+#pragma once
+#include <string.h>
+
+#include "impl.h"
+#include "kernels.cuh"
+
+namespace swept {
+
+template <typename T, class Op>
+struct Launch {
+  static typename Op::K kc(const void* k) {
+    typename Op::K kk;
+    memcpy(&kk, k, sizeof(kk));
+    return kk;
+  }
+  static int64_t smem_values(int M) { return swept_smem_values<Op>(M); }
+  static cudaError_t prepare(size_t bytes) {
+    cudaError_t e = cudaFuncSetAttribute(k_swept_up<T, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_swept_diamond<T, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  }
+  static cudaError_t up(const Geom& g, const void* k, const void* u_in, void* u_out, void* e_out, int hh,
+                        int write_top, int threads, size_t smem, cudaStream_t s) {
+    k_swept_up<T, Op><<<(unsigned)g.nt, threads, smem, s>>>(g, kc(k), (const T*)u_in, (T*)u_out, (T*)e_out, hh,
+                                                            write_top);
+    return cudaGetLastError();
+  }
+  static cudaError_t diamond(const Geom& g, const void* k, void* u_out, const void* e_in, void* e_out, int odd,
+                             int mode, int hh, int threads, size_t smem, cudaStream_t s) {
+    k_swept_diamond<T, Op><<<(unsigned)g.nt, threads, smem, s>>>(g, kc(k), (T*)u_out, (const T*)e_in, (T*)e_out, odd,
+                                                                 mode, hh);
+    return cudaGetLastError();
+  }
+  static cudaError_t classic(const Geom& g, const void* k, int stage, const void* in, void* out, cudaStream_t s) {
+    const int B = 256;
+    const unsigned grid = (unsigned)((g.N + B - 1) / B);
+    if (stage == 0)
+      k_classic<T, Op, 0><<<grid, B, 0, s>>>(g.N, g.bc, kc(k), (const T*)in, (T*)out);
+    else
+      k_classic<T, Op, 1><<<grid, B, 0, s>>>(g.N, g.bc, kc(k), (const T*)in, (T*)out);
+    return cudaGetLastError();
+  }
+  static cudaError_t copy(int64_t n, const void* src, void* dst, cudaStream_t s) {
+    k_copy<T><<<1024, 256, 0, s>>>(n, (const T*)src, (T*)dst);
+    return cudaGetLastError();
+  }
+};
+
+}  // namespace swept

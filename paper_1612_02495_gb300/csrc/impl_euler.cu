@@ -1,0 +1,45 @@
+// 1D Euler (MUSCL-minmod + Rusanov + SSP-RK2) instantiation of the kernels.
+#include "impl_common.cuh"
+
+namespace swept {
+namespace {
+
+// gamma, gamma - 1, 1/(gamma - 1), -dt/dx: computed in double, rounded to T.
+template <typename T>
+void euler_consts(const double* param, double dx, double dt, void* kbuf) {
+  typename EulerOp<T>::K k;
+  k.gamma = (T)param[0];
+  k.gm1 = (T)(param[0] - 1.0);
+  k.igm1 = (T)(1.0 / (param[0] - 1.0));
+  k.mdtdx = (T)(-(dt / dx));
+  memcpy(kbuf, &k, sizeof(k));
+}
+
+template <typename T>
+cudaError_t euler_classic(const Geom& g, const void* kb, int stage, const void* in, void* out, cudaStream_t s) {
+  const int B = 256;
+  const unsigned grid = (unsigned)((g.N + B - 1) / B);
+  const size_t smem = sizeof(T) * (3 * (B + 4) + 3 * (B + 1));
+  const auto k = Launch<T, EulerOp<T>>::kc(kb);
+  if (stage == 0)
+    k_classic_euler<T, 0><<<grid, B, smem, s>>>(g.N, g.bc, k, (const T*)in, (T*)out);
+  else
+    k_classic_euler<T, 1><<<grid, B, smem, s>>>(g.N, g.bc, k, (const T*)in, (T*)out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+SchemeImpl make_euler() {
+  using L = Launch<T, EulerOp<T>>;
+  return SchemeImpl{2, 2, 3, (int)sizeof(T), euler_consts<T>, L::smem_values, L::prepare, L::up, L::diamond,
+                    euler_classic<T>, L::copy};
+}
+
+const SchemeImpl kEulerF32 = make_euler<float>();
+const SchemeImpl kEulerF64 = make_euler<double>();
+
+}  // namespace
+
+const SchemeImpl* euler_impl(int dtype) { return dtype == 0 ? &kEulerF32 : &kEulerF64; }
+
+}  // namespace swept

@@ -1,0 +1,157 @@
+// Per-point stencil operators of the three schemes, in a fixed operation order.
+//
+// Every floating-point operation is an explicit round-to-nearest intrinsic
+// (__fma_rn, __dadd_rn, __dmul_rn, __ddiv_rn, __dsqrt_rn and the float forms),
+// so the compiler cannot contract or reorder them; the swept kernels and the
+// classic kernels call the same operator, which is what makes the two paths
+// agree bit for bit.  Constants are stored and multiplied instead of divided by
+// (Section "Results", Fig. divisionComparison).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "swept_geom.cuh"
+
+namespace swept {
+
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float sqrt_rn(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ double sqrt_rn(double a) { return __dsqrt_rn(a); }
+
+// ---------------------------------------------------------------------------
+// Heat, FTCS (Eq. HeatDisc): T' = Fo (T_{i+1} + T_{i-1}) + (1 - 2 Fo) T_i
+// order: s = T_{i+1} + T_{i-1};  T' = fma(Fo, s, c1 * T_i)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct HeatOp {
+  static constexpr int R = 1, S = 1, C = 1;
+  struct K {
+    T fo, c1;
+  };
+  // v[0..2] = T_{i-1}, T_i, T_{i+1} at the previous tier
+  template <int STAGE>
+  __device__ __forceinline__ static T point(const T* v, T /*prev2*/, const K& k) {
+    const T s = add_rn(v[2], v[0]);
+    return fma_rn(k.fo, s, mul_rn(k.c1, v[1]));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Kuramoto-Sivashinsky, Eq. KSDisc (u_i term read as -2 u_i, factor nu on the
+// fourth difference), midpoint RK2 (Appendix).  f = -g with
+//   sp1 = u_{i+1} + u_{i-1};  sp2 = u_{i+2} + u_{i-2}
+//   nl  = fma(u_{i+1}, u_{i+1}, -(u_{i-1} u_{i-1}))
+//   d2  = fma(-2, u_i, sp1);  d4 = fma(6, u_i, fma(-4, sp1, sp2))
+//   g   = fma(c_4, d4, fma(c_2, d2, c_a nl))
+// stage 0 (predictor, odd tiers):  P  = fma(-dt/2, g(u), u_i)
+// stage 1 (final, even tiers):     u' = fma(-dt,   g(P), u_i)   u_i from two tiers back
+// ---------------------------------------------------------------------------
+template <typename T>
+struct KsOp {
+  static constexpr int R = 2, S = 2, C = 1;
+  struct K {
+    T ca, c2, c4, mdth, mdt;
+  };
+  __device__ __forceinline__ static T g(const T* v, const K& k) {
+    const T sp1 = add_rn(v[3], v[1]);
+    const T sp2 = add_rn(v[4], v[0]);
+    const T nl = fma_rn(v[3], v[3], -mul_rn(v[1], v[1]));
+    const T d2 = fma_rn(T(-2), v[2], sp1);
+    const T d4 = fma_rn(T(6), v[2], fma_rn(T(-4), sp1, sp2));
+    return fma_rn(k.c4, d4, fma_rn(k.c2, d2, mul_rn(k.ca, nl)));
+  }
+  // v[0..4] = u_{i-2} .. u_{i+2} at the previous tier; prev2 = u_i two tiers back
+  template <int STAGE>
+  __device__ __forceinline__ static T point(const T* v, T prev2, const K& k) {
+    if (STAGE == 0) return fma_rn(k.mdth, g(v, k), v[2]);
+    return fma_rn(k.mdt, g(v, k), prev2);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// 1D Euler, finite volume (not in the paper): MUSCL-minmod on primitives,
+// Rusanov flux, SSP-RK2.  Order (per face i+1/2 from cells i-1..i+2):
+//   cell:   u = m / rho;  p = gm1 fma(-(0.5 m), u, E)
+//   qL = q_i + 0.5 minmod(q_i - q_{i-1}, q_{i+1} - q_i)
+//   qR = q_{i+1} - 0.5 minmod(q_{i+1} - q_i, q_{i+2} - q_{i+1})
+//   mX = rhoX uX;  EX = fma(0.5 mX, uX, pX igm1);  cX = sqrt((gamma pX) / rhoX)
+//   s  = max(|uL| + cL, |uR| + cR)
+//   F  = 0.5 fma(-s, UR - UL, FL + FR),  F = (m, fma(m, u, p), u (E + p))
+//   stage 0:  U1 = fma(-dt/dx, F+ - F-, U)
+//   stage 1:  t = fma(-dt/dx, F+ - F-, U1);  U' = 0.5 (U + t)
+// Across a reflective wall a cell is read as its mirror with u negated.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T minmod(T a, T b) {
+  if (a > T(0) && b > T(0)) return a <= b ? a : b;
+  if (a < T(0) && b < T(0)) return a >= b ? a : b;
+  return T(0);
+}
+
+template <typename T>
+struct EulerOp {
+  static constexpr int R = 2, S = 2, C = 3;
+  struct K {
+    T gamma, gm1, igm1, mdtdx;
+  };
+  struct Prim {
+    T r, u, p;
+  };
+  __device__ __forceinline__ static Prim prim(T r, T m, T e, const K& k) {
+    Prim w;
+    w.r = r;
+    w.u = div_rn(m, r);
+    w.p = mul_rn(k.gm1, fma_rn(-mul_rn(T(0.5), m), w.u, e));
+    return w;
+  }
+  // Rusanov flux through the face between cells b and c, from cells a, b, c, d
+  __device__ __forceinline__ static void flux(const Prim& a, const Prim& b, const Prim& c, const Prim& d, const K& k,
+                                              T& F0, T& F1, T& F2) {
+    Prim L, Rt;
+    {
+      const T dl = sub_rn(b.r, a.r), dc = sub_rn(c.r, b.r), dr = sub_rn(d.r, c.r);
+      L.r = add_rn(b.r, mul_rn(T(0.5), minmod(dl, dc)));
+      Rt.r = sub_rn(c.r, mul_rn(T(0.5), minmod(dc, dr)));
+    }
+    {
+      const T dl = sub_rn(b.u, a.u), dc = sub_rn(c.u, b.u), dr = sub_rn(d.u, c.u);
+      L.u = add_rn(b.u, mul_rn(T(0.5), minmod(dl, dc)));
+      Rt.u = sub_rn(c.u, mul_rn(T(0.5), minmod(dc, dr)));
+    }
+    {
+      const T dl = sub_rn(b.p, a.p), dc = sub_rn(c.p, b.p), dr = sub_rn(d.p, c.p);
+      L.p = add_rn(b.p, mul_rn(T(0.5), minmod(dl, dc)));
+      Rt.p = sub_rn(c.p, mul_rn(T(0.5), minmod(dc, dr)));
+    }
+    const T mL = mul_rn(L.r, L.u);
+    const T mR = mul_rn(Rt.r, Rt.u);
+    const T EL = fma_rn(mul_rn(T(0.5), mL), L.u, mul_rn(L.p, k.igm1));
+    const T ER = fma_rn(mul_rn(T(0.5), mR), Rt.u, mul_rn(Rt.p, k.igm1));
+    const T cL = sqrt_rn(div_rn(mul_rn(k.gamma, L.p), L.r));
+    const T cR = sqrt_rn(div_rn(mul_rn(k.gamma, Rt.p), Rt.r));
+    const T sL = add_rn(fabs(L.u), cL);
+    const T sR = add_rn(fabs(Rt.u), cR);
+    const T s = sL >= sR ? sL : sR;
+    F0 = mul_rn(T(0.5), fma_rn(-s, sub_rn(Rt.r, L.r), add_rn(mL, mR)));
+    F1 = mul_rn(T(0.5), fma_rn(-s, sub_rn(mR, mL), add_rn(fma_rn(mL, L.u, L.p), fma_rn(mR, Rt.u, Rt.p))));
+    F2 = mul_rn(T(0.5),
+                fma_rn(-s, sub_rn(ER, EL), add_rn(mul_rn(L.u, add_rn(EL, L.p)), mul_rn(Rt.u, add_rn(ER, Rt.p)))));
+  }
+  template <int STAGE>
+  __device__ __forceinline__ static T update(T fp, T fm, T in_self, T prev2, const K& k) {
+    if (STAGE == 0) return fma_rn(k.mdtdx, sub_rn(fp, fm), in_self);
+    const T t = fma_rn(k.mdtdx, sub_rn(fp, fm), in_self);
+    return mul_rn(T(0.5), add_rn(prev2, t));
+  }
+};
+
+}  // namespace swept

@@ -1,0 +1,36 @@
+// Handle state shared by the runtime (api.cu) and the host schedule checker
+// (check.cpp).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "swept.h"
+#include "impl.h"
+
+struct swept_handle {
+  swept_config cfg;
+  swept::Geom g;
+  const swept::SchemeImpl* impl = nullptr;
+  unsigned char k[swept::KBYTES];
+  int threads = 0;
+  size_t smem = 0;
+  int device = 0;
+  int sm_count = 0;
+  // workspace (caller-owned device memory)
+  char* ws = nullptr;
+  size_t ws_bytes = 0;   // required
+  size_t ws_bound = 0;   // bound size
+  size_t off_e0 = 0, off_e1 = 0, off_tmp = 0, off_status = 0;
+  // CUDA graphs cached by key; captured on a private stream
+  cudaStream_t cap = nullptr;
+  std::map<std::string, cudaGraphExec_t> graphs;
+  std::string err;
+};
+
+namespace swept {
+// symbolic replay of the swept launch sequence (check.cpp)
+swept_status check_schedule(swept_handle* h, int64_t nsteps, int64_t* computed);
+}  // namespace swept

@@ -1,0 +1,106 @@
+// Index arithmetic of the swept rule (shared by the CUDA kernels and the
+// host-side schedule checker, so the checker replays exactly what the kernels do).
+//
+// Swept rule (Magee & Niemeyer, Section "First-order", Figs. firstorder and
+// collection; Section "Second-order extended stencil", Fig. secondordersolution):
+//   - a tile ("node") of W points is advanced as a triangle: sub-timestep s is
+//     computed on the points whose radius-R stencil at s-1 is still inside the
+//     tile, i.e. the tile shrinks by R on each side per sub-timestep;
+//   - the 2R values at each end of every tier are the "edges" written to the
+//     global left/right arrays; a tier's values survive in a two-row buffer
+//     (even tiers in row 0, odd tiers in row 1) because the interior of row
+//     s&1 is overwritten only by tier s+2, which is narrower by 2R per side;
+//   - the next pass centres a block on each tile boundary c, re-inserts the
+//     left tile's right edges and the right tile's left edges, grows the
+//     complementary triangle on [c - R s, c + R s) up to s = h = W/(2R), where
+//     it spans a whole tile shifted by W/2, and then shrinks that tile again;
+//   - passes alternate between boundaries at (b+1) W (odd pass: tiles move
+//     right by W/2) and b W + W/2 (even pass: tiles move back), the zig-zag.
+// Local coordinates: a block's window is M = W + 2R points; a tile sits at
+// local [R, W + R); a diamond window centred on c sits at global
+// [c - W/2 - R, c + W/2 + R).
+#pragma once
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define SW_HD __host__ __device__ __forceinline__
+#else
+#define SW_HD inline
+#endif
+
+namespace swept {
+
+constexpr int NO_WALL = -(1 << 30);
+
+enum PassMode : int { MODE_DIAMOND = 0, MODE_DOWN = 1, MODE_GAP = 2 };
+
+struct Geom {
+  int64_t N;   // grid points
+  int64_t nt;  // tiles, N / W
+  int W;       // tile width
+  int R;       // stencil radius of one sub-timestep
+  int S;       // sub-timesteps (stages) per timestep
+  int C;       // values per point
+  int h;       // W / (2R): sub-timesteps per pass
+  int M;       // W + 2R: window width
+  int E;       // values per tile in an edge buffer: 2 sides * h * C * 2R
+  int bc;      // 0 periodic, 1 mirror walls at -1/2 and N-1/2
+};
+
+SW_HD int64_t floor_div(int64_t a, int64_t b) {
+  int64_t q = a / b;
+  return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
+}
+
+SW_HD int64_t wrap_n(int64_t x, int64_t n) {
+  int64_t r = x % n;
+  return r < 0 ? r + n : r;
+}
+
+// stage (0-based) of the update that produces sub-timestep level s >= 1
+SW_HD int stage_of(const Geom& g, int s) { return (s - 1) % g.S; }
+
+// tile tiers: level s on local [R + R s, W + R - R s)
+SW_HD int up_lo(const Geom& g, int s) { return g.R + g.R * s; }
+SW_HD int up_hi(const Geom& g, int s) { return g.W + g.R - g.R * s; }
+// complementary (growing) triangle: level s on local [W/2 + R - R s, W/2 + R + R s)
+SW_HD int grow_lo(const Geom& g, int s) { return g.W / 2 + g.R - g.R * s; }
+SW_HD int grow_hi(const Geom& g, int s) { return g.W / 2 + g.R + g.R * s; }
+
+// edge k (0..2R-1) of level s of a tile, side 0 = left end, 1 = right end
+SW_HD int edge_pos(const Geom& g, int side, int s, int k) {
+  return side == 0 ? g.R + g.R * s + k : g.W - g.R - g.R * s + k;
+}
+// where an edge lands in the diamond window: the right edges (side 1) of the
+// tile left of c, and the left edges (side 0) of the tile right of c
+SW_HD int insert_pos(const Geom& g, int side, int s, int k) {
+  return side == 1 ? g.W / 2 - g.R - g.R * s + k : g.W / 2 + g.R + g.R * s + k;
+}
+// offset of an edge value in an edge buffer (per tile block of E values)
+SW_HD int64_t edge_index(const Geom& g, int64_t tile, int side, int s, int c, int k) {
+  return tile * (int64_t)g.E + ((int64_t)(side * g.h + s) * g.C + c) * (2 * g.R) + k;
+}
+
+// pass p >= 1: boundary (diamond centre) handled by block b, and its two tiles
+SW_HD int64_t pass_center(const Geom& g, int odd, int64_t b) {
+  return odd ? (b + 1) * (int64_t)g.W : b * (int64_t)g.W + g.W / 2;
+}
+SW_HD int64_t left_tile(const Geom& g, int odd, int64_t b) { return odd ? b : (b + g.nt - 1) % g.nt; }
+SW_HD int64_t right_tile(const Geom& g, int odd, int64_t b) { return odd ? (b + 1) % g.nt : b; }
+
+// Local index of the first point after a mirror wall (x = k N) inside the
+// window [origin, origin + M), or NO_WALL (periodic, or no wall inside).
+SW_HD int window_wall(const Geom& g, int64_t origin) {
+  if (g.bc == 0) return NO_WALL;
+  const int64_t xw = (floor_div(origin, g.N) + 1) * g.N;
+  return (xw < origin + g.M) ? (int)(xw - origin) : NO_WALL;
+}
+// position read for neighbour offset d of point j: across a wall, the mirror
+// image (the boundary rule applied at the split node, Section "First-order")
+SW_HD int nbr(int j, int d, int wall) {
+  const int q = j + d;
+  return (wall != NO_WALL && ((j < wall) != (q < wall))) ? 2 * wall - 1 - q : q;
+}
+SW_HD bool through_wall(int j, int d, int wall) { return wall != NO_WALL && ((j < wall) != (j + d < wall)); }
+
+}  // namespace swept

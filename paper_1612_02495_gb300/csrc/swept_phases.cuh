@@ -1,0 +1,132 @@
+// The work of one block in one swept pass, written once over an execution
+// context `Cx`.  The CUDA kernels instantiate it with a device context (real
+// arithmetic in shared memory, __syncthreads between tiers); the host-side
+// schedule checker instantiates it with a symbolic context that tracks which
+// (point, sub-timestep) every buffer cell holds.
+//
+// Context interface (all indices local to the block's window unless noted):
+//   for_range(lo, hi, f)           f(i) for i in [lo, hi), spread over the block
+//   sync()                         block-wide barrier
+//   load_u(row, c, j, x)           window[row][c][j] = u[c][x mod N]
+//   store_u(row, c, j, x)          u[c][x mod N] = window[row][c][j]
+//   load_edge(row, c, j, e)        window[row][c][j] = edges_in[e]
+//   store_edge(row, c, j, e)       edges_out[e] = window[row][c][j]
+//   level(s, base, lo, hi, origin, wall)
+//                                  compute sub-timestep (base + s) on [lo, hi)
+//                                  into row s&1 from row (s-1)&1 (and row s&1
+//                                  for the second stage), then sync
+#pragma once
+#include "swept_geom.cuh"
+
+namespace swept {
+
+// Up-triangle (pass 0, Fig. SweptPseudo) or, with hh < h, the trapezoid that
+// starts the remainder: load tile b from u, compute tiers 1..hh, export the
+// 2R edge values of tiers 0..hh-1 on both sides; with write_top, also write
+// tier hh (the trapezoid's top, non-empty when hh < h) back to u.
+template <class Cx>
+SW_HD void run_up(Cx& cx, const Geom& g, int64_t b, int hh, bool write_top) {
+  const int64_t x0 = b * (int64_t)g.W;
+  const int64_t origin = x0 - g.R;
+  cx.for_range(0, g.W * g.C, [&](int i) {
+    const int c = i / g.W, k = i - c * g.W;
+    cx.load_u(0, c, g.R + k, x0 + k);
+  });
+  cx.sync();
+  for (int s = 1; s <= hh; ++s) cx.level(s, 0, up_lo(g, s), up_hi(g, s), origin, NO_WALL);
+  const int per_level = g.C * 2 * g.R;
+  const int per_side = hh * per_level;
+  cx.for_range(0, 2 * per_side, [&](int i) {
+    const int side = i / per_side;
+    const int rem = i - side * per_side;
+    const int s = rem / per_level;
+    const int c = (rem - s * per_level) / (2 * g.R);
+    const int k = rem % (2 * g.R);
+    cx.store_edge(s & 1, c, edge_pos(g, side, s, k), edge_index(g, b, side, s, c, k));
+  });
+  if (write_top) {
+    const int lo = up_lo(g, hh), w = up_hi(g, hh) - lo;
+    if (w > 0)
+      cx.for_range(0, w * g.C, [&](int i) {
+        const int c = i / w, k = i - c * w;
+        cx.store_u(hh & 1, c, lo + k, origin + lo + k);
+      });
+  }
+}
+
+// Diamond pass p >= 1 for block b (odd = p & 1): insert the neighbouring
+// tiles' edges (Fig. extraction), grow the complementary triangle for hh tiers.
+//   MODE_DIAMOND: then shrink the new tile (tiers 1..h-1 relative to it) and
+//                 export its edges to tile slot b of edges_out;
+//   MODE_DOWN:    write the completed tier h of the new tile to u (the only
+//                 point where a full tier exists, Section "First-order");
+//   MODE_GAP:     hh < h, write the grown gap [c - R hh, c + R hh) of tier hh
+//                 (completes the remainder trapezoids).
+template <class Cx>
+SW_HD void run_diamond(Cx& cx, const Geom& g, int64_t b, int odd, int mode, int hh) {
+  const int64_t c = pass_center(g, odd, b);
+  const int64_t origin = c - g.W / 2 - g.R;
+  const int64_t tl = left_tile(g, odd, b);
+  const int64_t tr = right_tile(g, odd, b);
+  const int per_level = g.C * 2 * g.R;
+  const int per_side = hh * per_level;
+  cx.for_range(0, 2 * per_side, [&](int i) {
+    const int which = i / per_side;  // 0: right edges of the left tile, 1: left edges of the right tile
+    const int rem = i - which * per_side;
+    const int s = rem / per_level;
+    const int cc = (rem - s * per_level) / (2 * g.R);
+    const int k = rem % (2 * g.R);
+    const int side = which == 0 ? 1 : 0;
+    const int64_t tile = which == 0 ? tl : tr;
+    cx.load_edge(s & 1, cc, insert_pos(g, side, s, k), edge_index(g, tile, side, s, cc, k));
+  });
+  cx.sync();
+  const int wall = window_wall(g, origin);
+  for (int s = 1; s <= hh; ++s) cx.level(s, 0, grow_lo(g, s), grow_hi(g, s), origin, wall);
+  if (mode == MODE_DIAMOND) {
+    for (int s = 1; s < g.h; ++s) cx.level(s, g.h, up_lo(g, s), up_hi(g, s), origin, wall);
+    const int per_side_h = g.h * per_level;
+    cx.for_range(0, 2 * per_side_h, [&](int i) {
+      const int side = i / per_side_h;
+      const int rem = i - side * per_side_h;
+      const int s = rem / per_level;
+      const int cc = (rem - s * per_level) / (2 * g.R);
+      const int k = rem % (2 * g.R);
+      cx.store_edge(s & 1, cc, edge_pos(g, side, s, k), edge_index(g, b, side, s, cc, k));
+    });
+  } else if (mode == MODE_DOWN) {
+    cx.for_range(0, g.W * g.C, [&](int i) {
+      const int cc = i / g.W, k = i - cc * g.W;
+      cx.store_u(g.h & 1, cc, g.R + k, origin + g.R + k);
+    });
+  } else {
+    const int lo = grow_lo(g, hh), w = grow_hi(g, hh) - lo;
+    cx.for_range(0, w * g.C, [&](int i) {
+      const int cc = i / w, k = i - cc * w;
+      cx.store_u(hh & 1, cc, lo + k, origin + lo + k);
+    });
+  }
+}
+
+// The launch sequence for n_sub sub-timesteps: q = n_sub / h full passes
+// (up, q-1 diamonds, down) and, for rem = n_sub % h, an up-trapezoid and a
+// gap pass.  `emit(kind, odd, mode, hh, pass)` is called once per launch:
+//   kind 0 = up (run_up), kind 1 = diamond (run_diamond).
+// The edge buffer written by pass k is k & 1 (ping-pong); the remainder pair
+// uses buffer 0 -> read by its gap pass.
+template <class F>
+inline void for_each_launch(const Geom& g, int64_t n_sub, F emit) {
+  const int64_t q = n_sub / g.h;
+  const int rem = (int)(n_sub % g.h);
+  if (q > 0) {
+    emit(0, 0, MODE_DIAMOND, g.h, (int64_t)0);
+    for (int64_t p = 1; p < q; ++p) emit(1, (int)(p & 1), MODE_DIAMOND, g.h, p);
+    emit(1, (int)(q & 1), MODE_DOWN, g.h, q);
+  }
+  if (rem > 0) {
+    emit(0, 0, MODE_GAP, rem, (int64_t)-1);
+    emit(1, 1, MODE_GAP, rem, (int64_t)-2);
+  }
+}
+
+}  // namespace swept

@@ -1,0 +1,208 @@
+"""Python binding of libswept.so (the C ABI declared in include/swept.h).
+
+Argument marshalling only: every step of the solver runs in the library's CUDA
+kernels.  PyTorch provides device memory and streams.  The binding refuses to
+load (ImportError) when libswept.so has not been built; there is no fallback.
+
+Functions with the C names take plain integers / pointers, exactly like the
+C ABI.  `Solver` is a small convenience owner of a handle plus a torch
+workspace tensor.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libswept.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libswept.so is not built (run __graft_entry__.build() or "
+                      "python -m paper_1612_02495_gb300.build); the CUDA path has no fallback")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# enums (include/swept.h)
+SWEPT_OK, SWEPT_EINVAL, SWEPT_ENOMEM_WORKSPACE, SWEPT_ECUDA = 0, 1, 2, 3
+SWEPT_ETIMEOUT, SWEPT_EUNSUPPORTED, SWEPT_ENOWORKSPACE, SWEPT_EDEVICE = 4, 5, 6, 7
+HEAT, KS, EULER = 0, 1, 2
+F32, F64 = 0, 1
+BC_PERIODIC, BC_REFLECTIVE = 0, 1
+
+STATUS_NAMES = {0: "SWEPT_OK", 1: "SWEPT_EINVAL", 2: "SWEPT_ENOMEM_WORKSPACE", 3: "SWEPT_ECUDA",
+                4: "SWEPT_ETIMEOUT", 5: "SWEPT_EUNSUPPORTED", 6: "SWEPT_ENOWORKSPACE", 7: "SWEPT_EDEVICE"}
+
+
+class swept_config(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int32), ("dtype", ctypes.c_int32), ("bc", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("n", ctypes.c_int64), ("dx", ctypes.c_double),
+                ("dt", ctypes.c_double), ("param", ctypes.c_double * 4), ("tile_w", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+
+class swept_plan_info(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int32), ("threads", ctypes.c_int32), ("half_cycle", ctypes.c_int32),
+                ("radius", ctypes.c_int32), ("stages", ctypes.c_int32), ("components", ctypes.c_int32),
+                ("tiles", ctypes.c_int64), ("smem_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64)]
+
+
+_H = ctypes.c_void_p
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_SZ = ctypes.c_size_t
+
+
+def _sig(name, args, res=ctypes.c_int):
+    f = getattr(_lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+swept_init = _sig("swept_init", [ctypes.POINTER(swept_config), ctypes.POINTER(_H)])
+swept_workspace_size = _sig("swept_workspace_size", [_H, ctypes.POINTER(_SZ)])
+swept_bind_workspace = _sig("swept_bind_workspace", [_H, _P, _SZ])
+swept_step_n = _sig("swept_step_n", [_H, _P, _I64, _P])
+classic_step_n = _sig("classic_step_n", [_H, _P, _I64, _P])
+swept_run_host = _sig("swept_run_host", [_H, _P, _P, _P, _I64, _I32, _P])
+swept_adjoint_ckpt_size = _sig("swept_adjoint_ckpt_size", [_H, _I64, ctypes.POINTER(_SZ)])
+swept_adjoint = _sig("swept_adjoint", [_H, _P, _P, _I64, _P, _P, _P, _SZ, _P])
+swept_profile_passes = _sig("swept_profile_passes", [_H, _P, _I64, _P, ctypes.POINTER(ctypes.c_double),
+                                                     ctypes.POINTER(_I64)])
+swept_get_plan = _sig("swept_get_plan", [_H, ctypes.POINTER(swept_plan_info)])
+swept_sync_status = _sig("swept_sync_status", [_H, _P])
+swept_check_schedule = _sig("swept_check_schedule", [_H, _I64, ctypes.POINTER(_I64)])
+swept_last_error = _sig("swept_last_error", [_H, ctypes.c_char_p, _SZ])
+swept_free = _sig("swept_free", [_H], None)
+
+
+class SweptError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def last_error(h):
+    buf = ctypes.create_string_buffer(512)
+    swept_last_error(h, buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def check(status, h=None, what=""):
+    if status != SWEPT_OK:
+        raise SweptError(status, (what + ": " if what else "") + (last_error(h) if h else ""))
+
+
+def make_config(scheme, dtype, n, dx, dt, param0, bc=BC_PERIODIC, tile_w=0, threads=0):
+    c = swept_config()
+    c.scheme, c.dtype, c.bc, c.n = int(scheme), int(dtype), int(bc), int(n)
+    c.dx, c.dt = float(dx), float(dt)
+    c.param[0] = float(param0)
+    c.tile_w, c.threads = int(tile_w), int(threads)
+    return c
+
+
+def init(cfg):
+    """swept_init -> handle (int); raises SweptError."""
+    h = _H()
+    st = swept_init(ctypes.byref(cfg), ctypes.byref(h))
+    if st != SWEPT_OK:
+        raise SweptError(st, "swept_init rejected the configuration")
+    return h.value
+
+
+def plan(h):
+    p = swept_plan_info()
+    check(swept_get_plan(h, ctypes.byref(p)), h, "swept_get_plan")
+    return {f: getattr(p, f) for f, _ in p._fields_}
+
+
+def check_schedule(h, nsteps):
+    """Host-only symbolic replay of the swept schedule; returns point updates performed."""
+    n = _I64()
+    check(swept_check_schedule(h, int(nsteps), ctypes.byref(n)), h, "swept_check_schedule")
+    return n.value
+
+
+def _stream_ptr(stream):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Solver:
+    """A handle plus its workspace (a torch uint8 tensor on the current device).
+
+    u tensors are contiguous torch tensors on the device with dtype float32 /
+    float64 matching `dtype`, shape (n,) for heat/KS and (3, n) for Euler.
+    """
+
+    def __init__(self, scheme, dtype, n, dx, dt, param0, bc=BC_PERIODIC, tile_w=0, threads=0):
+        import torch
+
+        self.cfg = make_config(scheme, dtype, n, dx, dt, param0, bc, tile_w, threads)
+        self.h = init(self.cfg)
+        self.scheme, self.dtype, self.n = scheme, dtype, n
+        self.torch_dtype = torch.float32 if dtype == F32 else torch.float64
+        sz = _SZ()
+        check(swept_workspace_size(self.h, ctypes.byref(sz)), self.h, "swept_workspace_size")
+        self.ws = torch.empty(int(sz.value), dtype=torch.uint8, device="cuda")
+        check(swept_bind_workspace(self.h, ctypes.c_void_p(self.ws.data_ptr()), sz.value), self.h,
+              "swept_bind_workspace")
+        self.plan = plan(self.h)
+
+    def _check_u(self, u):
+        if not u.is_cuda or not u.is_contiguous() or u.dtype != self.torch_dtype:
+            raise ValueError("u must be a contiguous CUDA tensor of dtype %s" % self.torch_dtype)
+        want = self.n * (3 if self.scheme == EULER else 1)
+        if u.numel() != want:
+            raise ValueError("u has %d values, expected %d" % (u.numel(), want))
+
+    def step(self, u, nsteps, stream=None):
+        """swept_step_n on u in place (asynchronous on the stream)."""
+        self._check_u(u)
+        check(swept_step_n(self.h, ctypes.c_void_p(u.data_ptr()), int(nsteps), _stream_ptr(stream)), self.h,
+              "swept_step_n")
+        return u
+
+    def classic(self, u, nsteps, stream=None):
+        """classic_step_n on u in place (asynchronous on the stream)."""
+        self._check_u(u)
+        check(classic_step_n(self.h, ctypes.c_void_p(u.data_ptr()), int(nsteps), _stream_ptr(stream)), self.h,
+              "classic_step_n")
+        return u
+
+    def run_host(self, u_host_in, u_host_out, u_dev, nsteps, use_swept=True, stream=None):
+        """swept_run_host: host tensors in/out (pinned for async copies), u_dev scratch on the device."""
+        self._check_u(u_dev)
+        check(swept_run_host(self.h, ctypes.c_void_p(u_host_in.data_ptr()), ctypes.c_void_p(u_host_out.data_ptr()),
+                             ctypes.c_void_p(u_dev.data_ptr()), int(nsteps), 1 if use_swept else 0,
+                             _stream_ptr(stream)), self.h, "swept_run_host")
+        return u_host_out
+
+    def profile_passes(self, u, nsteps, stream=None):
+        """swept_profile_passes: per-kind (ms, launches) for up, diamond, down, remainder."""
+        self._check_u(u)
+        ms = (ctypes.c_double * 4)()
+        cnt = (_I64 * 4)()
+        check(swept_profile_passes(self.h, ctypes.c_void_p(u.data_ptr()), int(nsteps), _stream_ptr(stream), ms, cnt),
+              self.h, "swept_profile_passes")
+        names = ("up", "diamond", "down", "remainder")
+        return {names[i]: (ms[i], cnt[i]) for i in range(4)}
+
+    def sync_status(self, stream=None):
+        check(swept_sync_status(self.h, _stream_ptr(stream)), self.h, "swept_sync_status")
+
+    def check_schedule(self, nsteps):
+        return check_schedule(self.h, nsteps)
+
+    def close(self):
+        if self.h:
+            swept_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

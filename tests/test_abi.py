@@ -1,0 +1,125 @@
+"""C-ABI library: loads, exports what include/swept.h declares, validates
+configurations, and its swept schedule passes the host-side symbolic check
+(no GPU work in this file)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1612_02495_gb300 import build as libbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def S():
+    libbuild.build()
+    from paper_1612_02495_gb300 import swept
+
+    return swept
+
+
+def declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:swept_status|void)\s+(\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(S):
+    names = declared_functions()
+    assert "swept_init" in names and "classic_step_n" in names and len(names) >= 12
+    lib = ctypes.CDLL(S.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_names_match_header(S):
+    for n in declared_functions():
+        assert hasattr(S, n), n
+
+
+def cfg(S, scheme=None, **kw):
+    base = dict(scheme=S.KS if scheme is None else scheme, dtype=S.F64, n=1024, dx=0.785, dt=0.005, param0=1.0)
+    base.update(kw)
+    return S.make_config(**base)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(n=0), dict(n=-5), dict(dx=0.0), dict(dt=-1.0), dict(tile_w=12), dict(tile_w=4096),
+    dict(tile_w=1000), dict(threads=48), dict(threads=2048), dict(dtype=7), dict(scheme=9),
+    dict(bc=1),  # KS is periodic only
+])
+def test_init_rejects_invalid_configs(S, bad):
+    c = cfg(S, **bad)
+    h = ctypes.c_void_p()
+    assert S.swept_init(ctypes.byref(c), ctypes.byref(h)) == S.SWEPT_EINVAL
+    assert not h.value
+
+
+def test_init_rejects_null(S):
+    h = ctypes.c_void_p()
+    assert S.swept_init(None, ctypes.byref(h)) == S.SWEPT_EINVAL
+
+
+def test_plan_report(S):
+    h = S.init(cfg(S, n=1 << 20))
+    p = S.plan(h)
+    assert p["radius"] == 2 and p["stages"] == 2 and p["components"] == 1
+    assert p["half_cycle"] * 2 * p["radius"] == p["tile_w"]
+    assert p["tiles"] * p["tile_w"] == 1 << 20
+    assert p["smem_bytes"] == 2 * (p["tile_w"] + 4) * 8
+    S.swept_free(h)
+
+
+def test_heat_config_plan(S):
+    h = S.init(S.make_config(S.HEAT, S.F64, 1024, 0.006, 1e-5, 1.0, tile_w=64))
+    p = S.plan(h)
+    assert p["tile_w"] == 64 and p["half_cycle"] == 32 and p["tiles"] == 16
+    S.swept_free(h)
+
+
+def test_compute_calls_fail_without_workspace(S):
+    h = S.init(cfg(S))
+    buf = ctypes.c_void_p(0x1000)
+    assert S.swept_step_n(h, buf, 10, None) == S.SWEPT_ENOWORKSPACE
+    assert S.classic_step_n(h, None, 10, None) == S.SWEPT_EINVAL
+    assert S.swept_step_n(h, buf, -1, None) == S.SWEPT_EINVAL
+    S.swept_free(h)
+
+
+def test_free_null_is_noop(S):
+    S.swept_free(None)
+
+
+SCHED = [
+    # scheme, bc, W, tiles
+    (0, 0, 4, 2), (0, 0, 8, 3), (0, 0, 16, 5), (0, 1, 4, 2), (0, 1, 8, 3), (0, 1, 32, 4),
+    (1, 0, 8, 2), (1, 0, 16, 3), (1, 0, 32, 5),
+    (2, 0, 8, 2), (2, 1, 8, 3), (2, 1, 16, 5), (2, 1, 32, 2),
+]
+
+
+@pytest.mark.parametrize("scheme,bc,W,nt", SCHED)
+def test_schedule_symbolic_replay(S, scheme, bc, W, nt):
+    """Every (point, sub-timestep) is computed once, after its stencil inputs,
+    with no race between blocks, for full passes, remainders and both BCs."""
+    n = W * nt
+    h = S.init(S.make_config(scheme, S.F64, n, 0.1, 1e-3, 1.4 if scheme == 2 else 1.0, bc=bc, tile_w=W))
+    Sst = 1 if scheme == 0 else 2
+    rr = 1 if scheme == 0 else 2
+    hh = W // (2 * rr)
+    for nsteps in sorted({0, 1, 2, 3, hh // Sst, hh // Sst + 1, 2 * hh // Sst + 1, 7 * hh // Sst + 3, 45}):
+        assert S.check_schedule(h, nsteps) == n * nsteps * Sst
+    S.swept_free(h)
+
+
+def test_schedule_large_pass_count(S):
+    """Enough passes to use the chunked graph path (head + repeated body + tail)."""
+    h = S.init(S.make_config(S.HEAT, S.F64, 64, 0.1, 1e-3, 1.0, tile_w=16))
+    assert S.check_schedule(h, 8 * 1100 + 5) == 64 * (8 * 1100 + 5)
+    S.swept_free(h)

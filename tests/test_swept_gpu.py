@@ -1,0 +1,184 @@
+"""GPU parity: the swept path and the classic path, called through the C ABI,
+against the CPU oracle on the same seeded inputs.
+
+Bar: the kernels evaluate every point with the oracle's operation order, so
+swept == classic == oracle bit for bit (which is within the stated bounds of
+1e-12 relative in FP64 and 1e-5 in FP32).  Cases span several tiles, odd tile
+counts, ragged step counts (a remainder of sub-timesteps after the last full
+pass), both boundary conditions, the minimum grid (two tiles) and the full
+workload sizes.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1612_02495_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+THREADS = max(1, min(32, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_1612_02495_gb300 import build as libbuild
+
+    libbuild.build()
+    from paper_1612_02495_gb300 import swept
+
+    return swept
+
+
+def relerr(a, ref):
+    a = np.asarray(a, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.max(np.abs(a - ref)) / np.max(np.abs(ref)))
+
+
+def run_gpu(S, scheme, dtype, u0, dx, dt, p0, nsteps, bc=0, tile_w=0, threads=0):
+    import torch
+
+    n = u0.shape[-1]
+    sol = S.Solver(scheme, dtype, n, dx, dt, p0, bc=bc, tile_w=tile_w, threads=threads)
+    u = torch.from_numpy(np.ascontiguousarray(u0)).cuda()
+    v = u.clone()
+    sol.step(u, nsteps)
+    sol.classic(v, nsteps)
+    torch.cuda.synchronize()
+    sol.sync_status()
+    out = u.cpu().numpy(), v.cpu().numpy(), sol.plan
+    sol.close()
+    return out
+
+
+def tol(dtype):
+    return 1e-12 if dtype == np.float64 else 1e-5
+
+
+# --------------------------------------------------------------------------- heat
+HEAT_CASES = [
+    # n, W, nsteps, bc
+    (1024, 64, 10000, 0),   # the full heat workload (N=1024, r=0.25, 10,000 steps, W=64)
+    (96, 16, 37, 0),        # ragged remainder
+    (40, 20, 0, 0),         # no-op
+    (40, 20, 1, 0),
+    (8 * 24, 8, 101, 1),    # insulated ends
+    (5 * 64, 64, 333, 1),   # odd tile count, insulated
+    (2 * 128, 128, 64 + 7, 0),  # minimum grid (two tiles)
+]
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("n,W,nsteps,bc", HEAT_CASES)
+def test_heat_parity(S, dtype, n, W, nsteps, bc):
+    p = inputs.heat_problem(n=n, dtype=dtype)
+    sw, cl, _ = run_gpu(S, S.HEAT, S.F64 if dtype == np.float64 else S.F32, p["u0"], p["dx"], p["dt"],
+                        p["alpha"], nsteps, bc=bc, tile_w=W)
+    ref = oracle.heat(p["u0"], p["dx"], p["dt"], p["alpha"], nsteps, bc=bc)
+    assert sw.dtype == dtype
+    assert np.array_equal(sw, cl), "swept != classic"
+    assert relerr(sw, ref) <= tol(dtype)
+    assert np.array_equal(sw, ref), "swept != oracle bitwise (relerr %g)" % relerr(sw, ref)
+
+
+# --------------------------------------------------------------------------- KS
+KS_CASES = [
+    # n, W, nsteps
+    (2048, 64, 1003),
+    (3 * 128, 128, 257),
+    (2 * 32, 32, 75),
+    (1 << 14, 0, 50000),    # the KS workload at N=2^14: full 50,000 steps, default plan
+    (1 << 16, 256, 2001),
+    (1 << 16, 1024, 600),   # largest tile
+]
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("n,W,nsteps", KS_CASES)
+def test_ks_parity(S, dtype, n, W, nsteps):
+    p = inputs.ks_problem(n=n, dtype=dtype)
+    sw, cl, plan = run_gpu(S, S.KS, S.F64 if dtype == np.float64 else S.F32, p["u0"], p["dx"], p["dt"], p["nu"],
+                           nsteps, tile_w=W)
+    ref = oracle.ks(p["u0"], p["dx"], p["dt"], p["nu"], nsteps, threads=THREADS)
+    assert np.array_equal(sw, cl), "swept != classic"
+    assert relerr(sw, ref) <= tol(dtype)
+    assert np.array_equal(sw, ref), "swept != oracle bitwise (relerr %g)" % relerr(sw, ref)
+
+
+@pytest.mark.parametrize("threads", [32, 64, 128, 256, 512])
+def test_ks_thread_counts(S, threads):
+    p = inputs.ks_problem(n=4096)
+    sw, cl, plan = run_gpu(S, S.KS, S.F64, p["u0"], p["dx"], p["dt"], p["nu"], 377, tile_w=512, threads=threads)
+    assert plan["threads"] == threads
+    ref = oracle.ks(p["u0"], p["dx"], p["dt"], p["nu"], 377, threads=THREADS)
+    assert np.array_equal(sw, cl) and np.array_equal(sw, ref)
+
+
+# --------------------------------------------------------------------------- Euler
+EULER_CASES = [
+    # n, W, nsteps, bc
+    (1024, 64, 300, 1),
+    (1024, 64, 300, 0),
+    (3 * 32, 32, 77, 1),
+    (2 * 8, 8, 13, 1),       # minimum tile and grid
+    (1 << 16, 0, 1000, 1),   # the Sod workload at N=2^16, 1,000-step window, default plan
+]
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("n,W,nsteps,bc", EULER_CASES)
+def test_euler_parity(S, dtype, n, W, nsteps, bc):
+    pr = inputs.euler_problem(n=n, dtype=dtype)
+    U0 = pr["U0"]
+    if bc == 0:  # periodic: a smooth travelling state instead of the tube
+        x = (np.arange(n) + 0.5) / n
+        rho = 1 + 0.2 * np.sin(2 * np.pi * x)
+        u = 0.3 + 0.1 * np.cos(2 * np.pi * x)
+        p = 1 + 0.1 * np.sin(4 * np.pi * x)
+        U0 = np.stack([rho, rho * u, p / 0.4 + 0.5 * rho * u * u]).astype(dtype)
+    sw, cl, _ = run_gpu(S, S.EULER, S.F64 if dtype == np.float64 else S.F32, U0, pr["dx"], pr["dt"], pr["gamma"],
+                        nsteps, bc=bc, tile_w=W)
+    ref = oracle.euler(U0, pr["dx"], pr["dt"], pr["gamma"], nsteps, bc=bc, threads=THREADS)
+    assert np.array_equal(sw, cl), "swept != classic"
+    assert relerr(sw, ref) <= tol(dtype)
+    assert np.array_equal(sw, ref), "swept != oracle bitwise (relerr %g)" % relerr(sw, ref)
+
+
+# --------------------------------------------------------------------------- full size, bench launch config
+def test_ks_full_size_sampled(S):
+    """KS N=2^20 FP64, 50,000 steps, default plan (the bench configuration):
+    swept == classic bit for bit; the mean is conserved; the whole field after
+    the first 100 steps equals the oracle; and sampled points of the final
+    state equal the oracle advanced 100 steps from the GPU state at 49,900
+    steps on a window covering their domain of dependence."""
+    import torch
+
+    n, total, tail = 1 << 20, 50000, 100
+    p = inputs.ks_problem(n=n)
+    sol = S.Solver(S.KS, S.F64, n, p["dx"], p["dt"], p["nu"])
+    u = torch.from_numpy(p["u0"]).cuda()
+    v, w = u.clone(), u.clone()
+    sol.step(u, total)
+    sol.classic(v, total)
+    sol.step(w, total - tail)
+    torch.cuda.synchronize()
+    sol.sync_status()
+    fin, fin_c, mid = u.cpu().numpy(), v.cpu().numpy(), w.cpu().numpy()
+    assert np.array_equal(fin, fin_c)
+    assert abs(fin.sum() - p["u0"].sum()) <= 1e-11 * np.abs(p["u0"]).sum()
+    # first 100 steps, full field
+    a = torch.from_numpy(p["u0"]).cuda()
+    sol.step(a, tail)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.cpu().numpy(), oracle.ks(p["u0"], p["dx"], p["dt"], p["nu"], tail, threads=THREADS))
+    # sampled final points: domain of dependence of 100 steps is 2 stages * 2 * 100 points per side
+    reach = 2 * 2 * tail
+    rng = inputs.rng(99)
+    for c in rng.integers(0, n, size=8):
+        idx = (np.arange(c - reach - 8, c + reach + 9)) % n
+        loc = oracle.ks(mid[idx], p["dx"], p["dt"], p["nu"], tail)  # periodic on the window; edges are garbage
+        k = reach + 8
+        assert loc[k] == fin[c], (c, loc[k], fin[c])
+    sol.close()
