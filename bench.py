@@ -32,6 +32,13 @@ UNIT = "cell-updates/s"
 WORKLOAD = "Kuramoto-Sivashinsky N=2^20 FP64 periodic, 50,000 midpoint-RK2 steps (dt=0.005, dx=pi/4)"
 FP64_FLOPS_PER_SUBSTEP = 18  # 7 fma (2 flops) + 2 add + 2 mul per point per sub-timestep
 FP64_INSTR_PER_SUBSTEP = 11
+# FP64 roof of GB300: 152 SMs x 2 DFMA per clock x 2 flops x 2.07 GHz (nominal 1.25 TFLOP/s);
+# the issue-rate probe measured 0.60e12 DFMA/s.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_INSTR_PEAK = 152 * 2 * 2.07e9
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_swept_diamond<double, KsOp> launch at
+# N = 2^20, tile 1024 (ncu, profiles/k_swept_diamond_ks_f64_n1048576.md); None once the kernel changes
+DIAMOND_TRAFFIC_BYTES = 16824832
 
 
 def peaks():
@@ -244,13 +251,13 @@ def main():
     d_ms, d_n = prof["diamond"]
     d_avg = d_ms / max(d_n, 1)
     flops_per_diamond = FP64_FLOPS_PER_SUBSTEP * N * plan["half_cycle"]
-    pk = peaks()
-    fp64_peak_tflops = 1.2  # measured DFMA rate 0.60 T/s x 2 flops (FP64 pipe, GB300)
     achieved = flops_per_diamond / (d_avg * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak_tflops, "traffic": None, "kernel": "k_swept_diamond<double, KsOp>",
-                "peak_source": "measured FP64 FMA issue rate on this GB300 (0.60e12 DFMA/s), x2 flops",
-                "pipe_frac": (FP64_INSTR_PER_SUBSTEP * N * plan["half_cycle"] / (d_avg * 1e-3)) / 0.60e12,
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": DIAMOND_TRAFFIC_BYTES,
+                "kernel": "k_swept_diamond<double, KsOp<double>>",
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured DFMA issue rate "
+                               "0.60e12/s = 1.20 TFLOP/s)",
+                "pipe_frac": (FP64_INSTR_PER_SUBSTEP * N * plan["half_cycle"] / (d_avg * 1e-3)) / FP64_INSTR_PEAK,
                 "diamond_ms_avg": d_avg, "diamond_share": d_ms / max(sum(v[0] for v in prof.values()), 1e-9)}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -1,0 +1,72 @@
+"""Run one solve of a configuration through the C ABI and print its time.
+
+  python -m paper_1612_02495_gb300.run_case --scheme ks --dtype f64 --n 1048576 \\
+      --nsteps 600 [--path swept|classic] [--tile 0] [--threads 0] [--repeat 1]
+
+Used to profile a single kernel on a chosen size (e.g. under ncu).  One
+untimed warm-up solve precedes the timed repeats.
+"""
+import argparse
+import json
+import sys
+
+import numpy as np
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--scheme", default="ks", choices=["heat", "ks", "euler"])
+    ap.add_argument("--dtype", default="f64", choices=["f32", "f64"])
+    ap.add_argument("--n", type=int, default=1 << 20)
+    ap.add_argument("--nsteps", type=int, default=600)
+    ap.add_argument("--path", default="swept", choices=["swept", "classic"])
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--repeat", type=int, default=1)
+    a = ap.parse_args(argv)
+
+    import torch
+
+    from . import inputs
+    from . import swept as S
+
+    npd = np.float64 if a.dtype == "f64" else np.float32
+    dt_code = S.F64 if a.dtype == "f64" else S.F32
+    if a.scheme == "heat":
+        p = inputs.heat_problem(n=a.n, dtype=npd)
+        args = (S.HEAT, dt_code, a.n, p["dx"], p["dt"], p["alpha"], S.BC_PERIODIC)
+        u0 = p["u0"]
+    elif a.scheme == "ks":
+        p = inputs.ks_problem(n=a.n, dtype=npd)
+        args = (S.KS, dt_code, a.n, p["dx"], p["dt"], p["nu"], S.BC_PERIODIC)
+        u0 = p["u0"]
+    else:
+        p = inputs.euler_problem(n=a.n, dtype=npd)
+        args = (S.EULER, dt_code, a.n, p["dx"], p["dt"], p["gamma"], S.BC_REFLECTIVE)
+        u0 = p["U0"]
+    sol = S.Solver(*args, tile_w=a.tile, threads=a.threads)
+    u_init = torch.from_numpy(np.ascontiguousarray(u0)).cuda()
+    u = u_init.clone()
+    run = sol.step if a.path == "swept" else sol.classic
+    run(u, a.nsteps)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(a.repeat):
+        u.copy_(u_init)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run(u, a.nsteps)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    sol.sync_status()
+    ms = float(np.median(times))
+    print(json.dumps({"scheme": a.scheme, "dtype": a.dtype, "n": a.n, "nsteps": a.nsteps, "path": a.path,
+                      "plan": sol.plan, "ms": ms,
+                      "cell_updates_per_s": a.n * a.nsteps / (ms * 1e-3)}))
+    sol.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
