@@ -158,6 +158,24 @@ swept_status swept_adjoint(swept_handle* h, const void* u0_dev, const void* gT_d
 swept_status swept_profile_passes(swept_handle* h, void* u_dev, int64_t nsteps, void* stream, double* out_ms,
                                   int64_t* out_count);
 
+/* Swept solve that allocates nothing, for callers that cannot call cudaMalloc
+ * (their device memory belongs to an outside memory manager, or they run in a
+ * loop where cudaMalloc/cudaFree would synchronise the device).  The paper has
+ * no counterpart; it is swept_step_n with the edge buffers in one fixed 8 MiB
+ * device array inside the library instead of a bound workspace, and without a
+ * handle, graph or stream of its own.
+ *   cfg      as for swept_init, except that tile_w must be set (> 0)
+ *   u_dev    caller-owned state (layout above), advanced nsteps in place
+ * The grid must fit the array: 4 * n * C * sizeof(value) <= 8 MiB (n <= 2^18 for
+ * FP64 heat/KS, 2^19 for FP32); larger grids return SWEPT_ENOMEM_WORKSPACE and
+ * launch nothing.  Results equal swept_step_n bit for bit.
+ * The first call on each device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every call
+ * shares the one array (it keeps the last call's contents), so calls that
+ * overlap on the GPU race; serialise them.
+ * Errors: SWEPT_EINVAL, SWEPT_ENOMEM_WORKSPACE, SWEPT_ECUDA. */
+swept_status swept_step_n_static(const swept_config* cfg, void* u_dev, int64_t nsteps, void* stream);
+
 /* Plan report. */
 swept_status swept_get_plan(const swept_handle* h, swept_plan_info* out);
 

@@ -68,6 +68,7 @@ swept_adjoint_ckpt_size = _sig("swept_adjoint_ckpt_size", [_H, _I64, ctypes.POIN
 swept_adjoint = _sig("swept_adjoint", [_H, _P, _P, _I64, _P, _P, _P, _SZ, _P])
 swept_profile_passes = _sig("swept_profile_passes", [_H, _P, _I64, _P, ctypes.POINTER(ctypes.c_double),
                                                      ctypes.POINTER(_I64)])
+swept_step_n_static = _sig("swept_step_n_static", [ctypes.POINTER(swept_config), _P, _I64, _P])
 swept_get_plan = _sig("swept_get_plan", [_H, ctypes.POINTER(swept_plan_info)])
 swept_sync_status = _sig("swept_sync_status", [_H, _P])
 swept_check_schedule = _sig("swept_check_schedule", [_H, _I64, ctypes.POINTER(_I64)])
