@@ -122,6 +122,50 @@ def cpu_oracle_rate(n, seconds, threads):
     return n * steps / dt, steps, dt
 
 
+def measure_adjoint(S, inputs, torch, stream, k, barrier):
+    """Adjoint workload: KS N=2^18 FP64, 5,000 steps.  Times (CUDA events, median of k)
+    the forward solve, the checkpointing forward, and the reverse sweep that continues
+    from it (dL/du0 and dL/dnu), with the default (sqrt) checkpoint memory."""
+    n, nsteps = 1 << 18, 5000
+    p = inputs.ks_problem(n=n, seed=71)
+    sol = S.Solver(S.KS, S.F64, n, p["dx"], p["dt"], p["nu"])
+    u0 = torch.from_numpy(p["u0"]).cuda()
+    u = u0.clone()
+    nb = sol.ckpt_size(nsteps)
+    ck = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    gT = torch.from_numpy(inputs.rng(72).standard_normal(n)).cuda()
+    g = torch.empty_like(gT)
+    gp = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    def ev(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        return a, b
+
+    res = {"fwd": [], "fwd_ckpt": [], "adj": []}
+    for i in range(k + 1):
+        u.copy_(u0)
+        e1 = ev(lambda: sol.step(u, nsteps))
+        u.copy_(u0)
+        e2 = ev(lambda: sol.forward_ckpt(u, nsteps, ck))
+        e3 = ev(lambda: sol.adjoint(gT, nsteps, ck, g_u0=g, g_param=gp))
+        barrier()
+        if i > 0:  # first round warms the graphs
+            for key, (a, b) in zip(("fwd", "fwd_ckpt", "adj"), (e1, e2, e3)):
+                res[key].append(a.elapsed_time(b))
+    sol.sync_status()
+    seg = sol.plan["half_cycle"] // sol.plan["stages"]
+    med = {key: float(np.median(v)) for key, v in res.items()}
+    sol.close()
+    return {"workload": "KS N=2^18 FP64, 5,000 steps, L = sum (u(T) - u_target)^2, grad wrt u0 and nu",
+            "forward_ms": med["fwd"], "forward_ckpt_ms": med["fwd_ckpt"], "adjoint_ms": med["adj"],
+            "adjoint_over_forward": med["adj"] / med["fwd"],
+            "forward_plus_adjoint_over_forward": (med["fwd_ckpt"] + med["adj"]) / med["fwd"],
+            "ckpt_bytes": nb, "steps_per_pass": seg}
+
+
 def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
@@ -160,6 +204,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-classic", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -260,6 +305,10 @@ def main():
                 "pipe_frac": (FP64_INSTR_PER_SUBSTEP * N * plan["half_cycle"] / (d_avg * 1e-3)) / FP64_INSTR_PEAK,
                 "diamond_ms_avg": d_avg, "diamond_share": d_ms / max(sum(v[0] for v in prof.values()), 1e-9)}
 
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = measure_adjoint(S, inputs, torch, stream, max(2, args.steps), barrier)
+
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -270,6 +319,8 @@ def main():
            "e2e": {"value": ws * N * NSTEPS / (e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": N * 8,
                    "d2h_bytes_per_step": N * 8},
            "roofline": roofline, "clocks": clk}
+    if adjoint:
+        out["adjoint"] = adjoint
     if ms_classic:
         out["classic"] = {"value": ws * N * NSTEPS / (ms_classic * 1e-3), "ms_per_step": ms_classic}
         out["speedup_vs_classic"] = ms_classic / ms

@@ -139,13 +139,27 @@ swept_status classic_step_n(swept_handle* h, void* u_dev, int64_t nsteps, void* 
 swept_status swept_run_host(swept_handle* h, const void* u_host_in, void* u_host_out, void* u_dev, int64_t nsteps,
                             int32_t use_swept, void* stream);
 
-/* Discrete adjoint of swept_step_n for SWEPT_KS and SWEPT_HEAT in SWEPT_F64.
- * Given u0_dev (the initial state) and gT_dev = dL/du(T) after nsteps steps,
- * writes g_u0_dev = dL/du0 and g_param_dev[0] = dL/dparam[0] (nu or alpha).
- * The forward states are recomputed from checkpoints stored in ckpt_dev
- * (size from swept_adjoint_ckpt_size).  Not in the paper.
- * Errors: SWEPT_EUNSUPPORTED (scheme/dtype), SWEPT_EINVAL, SWEPT_ENOMEM_WORKSPACE. */
+/* Discrete adjoint of swept_step_n for SWEPT_KS and SWEPT_HEAT in SWEPT_F64
+ * (not in the paper).  The loss L depends on u(T), the state after nsteps
+ * steps from u0; given gT_dev = dL/du(T) it writes g_u0_dev = dL/du0 (layout of
+ * u) and g_param_dev[0] = dL/dparam[0] (nu for KS, alpha for heat), one double.
+ * The reverse sweep runs the swept schedule backwards with the transposed
+ * stencil (same radius and tiers); each tier reads the forward state of its
+ * sub-timestep from a tape.  Forward states are recomputed segment by segment
+ * from checkpoints in ckpt_dev: u at the start of every segment of K steps,
+ * plus one segment's tape of S*K + 1 tiers.  K is the largest whole number of
+ * passes (h/S steps) whose layout fits ckpt_bytes; ckpt_bytes =
+ * swept_adjoint_ckpt_size() gives K near sqrt(nsteps * h/S), and a buffer
+ * large enough for K = nsteps stores the whole run and recomputes nothing.
+ * If u0_dev is NULL, the checkpoints and the last segment's tape written by the
+ * most recent swept_forward_ckpt on this handle (same ckpt_dev, ckpt_bytes,
+ * nsteps) are used, so only the earlier segments are recomputed; otherwise the
+ * checkpointing forward pass from u0_dev runs first.  g_u0_dev may alias
+ * gT_dev.  Errors: SWEPT_EUNSUPPORTED (scheme/dtype), SWEPT_EINVAL (no
+ * matching forward for u0_dev = NULL), SWEPT_ENOMEM_WORKSPACE (ckpt too small). */
 swept_status swept_adjoint_ckpt_size(const swept_handle* h, int64_t nsteps, size_t* bytes);
+swept_status swept_forward_ckpt(swept_handle* h, void* u_dev, int64_t nsteps, void* ckpt_dev, size_t ckpt_bytes,
+                                void* stream);
 swept_status swept_adjoint(swept_handle* h, const void* u0_dev, const void* gT_dev, int64_t nsteps, void* g_u0_dev,
                            void* g_param_dev, void* ckpt_dev, size_t ckpt_bytes, void* stream);
 

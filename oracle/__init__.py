@@ -43,8 +43,8 @@ def lib():
             getattr(L, "oracle_ks_run_" + sfx).argtypes = [_P, _I64, _D, _D, _D, _I64, _INT]
             getattr(L, "oracle_euler_run_" + sfx).argtypes = [_P, _I64, _D, _D, _D, _INT, _I64, _INT]
             getattr(L, "oracle_euler_stage_" + sfx).argtypes = [_P, _P, _I64, _D, _D, _D, _INT]
-        L.oracle_ks_adjoint_f64.argtypes = [_P, _I64, _D, _D, _D, _I64, _P, _P, _P, _I64]
-        L.oracle_heat_adjoint_f64.argtypes = [_P, _I64, _D, _D, _D, _INT, _I64, _P, _P, _P]
+        L.oracle_ks_adjoint_f64.argtypes = [_P, _I64, _D, _D, _D, _I64, _P, _P, _P, _I64, _P]
+        L.oracle_heat_adjoint_f64.argtypes = [_P, _I64, _D, _D, _D, _INT, _I64, _P, _P, _P, _P]
         L.oracle_max_threads.restype = _INT
         _lib = L
     return _lib
@@ -107,23 +107,25 @@ def euler_stage(U0, dx, dt, gamma, bc=BC_MIRROR):
     return out
 
 
-def ks_adjoint(u0, dx, dt, nu, nsteps, gT, seg=0):
-    """Discrete adjoint of `ks` (FP64): returns (dL/du0, dL/dnu) for dL/du(T) = gT."""
+def ks_adjoint(u0, dx, dt, nu, nsteps, gT, seg=0, with_condition=False):
+    """Discrete adjoint of `ks` (FP64): returns (dL/du0, dL/dnu) for dL/du(T) = gT; with
+    with_condition, also the sum of the absolute values of dL/dnu's terms (its condition)."""
     u0 = np.ascontiguousarray(u0, dtype=np.float64)
     gT = np.ascontiguousarray(gT, dtype=np.float64)
     g = np.empty_like(u0)
-    gnu = np.zeros(1)
-    _check(lib().oracle_ks_adjoint_f64(_ptr(u0), u0.size, dx, dt, nu, nsteps, _ptr(gT), _ptr(g), _ptr(gnu), seg),
-           "ks_adjoint")
-    return g, float(gnu[0])
+    gnu = np.zeros(2)
+    _check(lib().oracle_ks_adjoint_f64(_ptr(u0), u0.size, dx, dt, nu, nsteps, _ptr(gT), _ptr(g), _ptr(gnu[0:]), seg,
+                                       _ptr(gnu[1:])), "ks_adjoint")
+    return (g, float(gnu[0]), float(gnu[1])) if with_condition else (g, float(gnu[0]))
 
 
-def heat_adjoint(u0, dx, dt, alpha, nsteps, gT, bc=BC_PERIODIC):
-    """Discrete adjoint of `heat` (FP64): returns (dL/du0, dL/dalpha) for dL/du(T) = gT."""
+def heat_adjoint(u0, dx, dt, alpha, nsteps, gT, bc=BC_PERIODIC, with_condition=False):
+    """Discrete adjoint of `heat` (FP64): returns (dL/du0, dL/dalpha) for dL/du(T) = gT; with
+    with_condition, also the sum of the absolute values of dL/dalpha's terms."""
     u0 = np.ascontiguousarray(u0, dtype=np.float64)
     gT = np.ascontiguousarray(gT, dtype=np.float64)
     g = np.empty_like(u0)
-    ga = np.zeros(1)
-    _check(lib().oracle_heat_adjoint_f64(_ptr(u0), u0.size, dx, dt, alpha, bc, nsteps, _ptr(gT), _ptr(g), _ptr(ga)),
-           "heat_adjoint")
-    return g, float(ga[0])
+    ga = np.zeros(2)
+    _check(lib().oracle_heat_adjoint_f64(_ptr(u0), u0.size, dx, dt, alpha, bc, nsteps, _ptr(gT), _ptr(g),
+                                         _ptr(ga[0:]), _ptr(ga[1:])), "heat_adjoint")
+    return (g, float(ga[0]), float(ga[1])) if with_condition else (g, float(ga[0]))

@@ -101,6 +101,10 @@ static inline int64_t nb_index(int64_t j, int64_t n, int bc, int* flip) {
  * Parameter derivative (c_4 = nu k4, k4 = 1/dx^4, dg/dnu = k4 d4(w)):
  *   dL/dnu = sum_m sum_j [ -dt lam'_j k4 d4(P)_j - (dt/2) mu_j k4 d4(u^m)_j ]
  * accumulated in long double in the order m descending, j ascending.
+ * Also returned: the same sum with every factor replaced by its absolute
+ * value and d4 by the absolute stencil |w_{j+2}| + 4|w_{j+1}| + 6|w_j| +
+ * 4|w_{j-1}| + |w_{j-2}| -- the condition of the sum, which bounds the
+ * rounding error of any evaluation of it that rounds each term a few times.
  */
 static inline double ks_gT(const double* lam, const double* w, int64_t j, int64_t n, double ca2, double c2,
                            double c4) {
@@ -118,6 +122,13 @@ static inline double ks_gT(const double* lam, const double* w, int64_t j, int64_
   return fma(c4, d4, fma(c2, d2, nl));
 }
 
+static inline long double ks_d4_abs(const double* w, int64_t j, int64_t n) {
+  return fabsl((long double)w[nb_index(j + 2, n, OR_BC_PERIODIC, NULL)]) +
+         4.0L * fabsl((long double)w[nb_index(j + 1, n, OR_BC_PERIODIC, NULL)]) + 6.0L * fabsl((long double)w[j]) +
+         4.0L * fabsl((long double)w[nb_index(j - 1, n, OR_BC_PERIODIC, NULL)]) +
+         fabsl((long double)w[nb_index(j - 2, n, OR_BC_PERIODIC, NULL)]);
+}
+
 static inline double ks_d4(const double* w, int64_t j, int64_t n) {
   const double sp1 = w[nb_index(j + 1, n, OR_BC_PERIODIC, NULL)] + w[nb_index(j - 1, n, OR_BC_PERIODIC, NULL)];
   const double sp2 = w[nb_index(j + 2, n, OR_BC_PERIODIC, NULL)] + w[nb_index(j - 2, n, OR_BC_PERIODIC, NULL)];
@@ -130,7 +141,7 @@ static inline double ks_d4(const double* w, int64_t j, int64_t n) {
  * every `seg` steps (seg <= 0: one segment holding every state).
  */
 int oracle_ks_adjoint_f64(const double* u0, int64_t n, double dx, double dt, double nu, int64_t nsteps,
-                          const double* gT, double* g_u0, double* g_nu, int64_t seg) {
+                          const double* gT, double* g_u0, double* g_nu, int64_t seg, double* g_nu_abs) {
   if (!u0 || !gT || !g_u0 || !g_nu || n < 5 || nsteps < 0) return -1;
   if (seg <= 0 || seg > nsteps) seg = nsteps > 0 ? nsteps : 1;
   const ks_consts_f64 k = ks_make_consts_f64(dx, dt, nu);
@@ -155,7 +166,7 @@ int oracle_ks_adjoint_f64(const double* u0, int64_t n, double dx, double dt, dou
     ks_step_f64(cur, mu, n, &k, 1);
   }
   memcpy(lam, gT, (size_t)n * sizeof(double));
-  long double acc = 0.0L;
+  long double acc = 0.0L, acc_abs = 0.0L;
   const int64_t nseg = (nsteps + seg - 1) / seg;
   for (int64_t s = nseg - 1; s >= 0; --s) {
     const int64_t m0 = s * seg;
@@ -177,6 +188,8 @@ int oracle_ks_adjoint_f64(const double* u0, int64_t n, double dx, double dt, dou
       for (int64_t j = 0; j < n; ++j) {
         acc += (long double)(-dt) * (long double)lam[j] * (long double)k4 * (long double)ks_d4(tp, j, n);
         acc += (long double)(-0.5 * dt) * (long double)mu[j] * (long double)k4 * (long double)ks_d4(tu, j, n);
+        acc_abs += (long double)dt * fabsl((long double)lam[j]) * (long double)k4 * ks_d4_abs(tp, j, n);
+        acc_abs += (long double)(0.5 * dt) * fabsl((long double)mu[j]) * (long double)k4 * ks_d4_abs(tu, j, n);
       }
       /* lam is read by the stencil, so compute into cur and copy back */
       for (int64_t j = 0; j < n; ++j) cur[j] = fma(k.mdth, ks_gT(mu, tu, j, n, ca2, k.c2, k.c4), lam[j] + mu[j]);
@@ -185,6 +198,7 @@ int oracle_ks_adjoint_f64(const double* u0, int64_t n, double dx, double dt, dou
   }
   memcpy(g_u0, lam, (size_t)n * sizeof(double));
   *g_nu = (double)acc;
+  if (g_nu_abs) *g_nu_abs = (double)acc_abs;
   free(ck); free(tape_u); free(tape_p); free(lam); free(mu); free(cur);
   return 0;
 }
@@ -195,10 +209,11 @@ int oracle_ks_adjoint_f64(const double* u0, int64_t n, double dx, double dt, dou
  *   lam_j = fma(Fo, lam'_{j+1} + lam'_{j-1}, c1 lam'_j)
  * (mirror boundaries: the transpose of "ghost -1 reads cell 0" adds the ghost's
  * weight back onto cell 0, which is again the mirror update).
- * dL/dalpha = sum_m sum_i lam'_i (dt/dx^2) (T_{i+1} + T_{i-1} - 2 T_i)^m.
+ * dL/dalpha = sum_m sum_i lam'_i (dt/dx^2) (T_{i+1} + T_{i-1} - 2 T_i)^m, and its
+ * condition sum_m sum_i |lam'_i| (dt/dx^2) (|T_{i+1}| + |T_{i-1}| + 2 |T_i|)^m.
  */
 int oracle_heat_adjoint_f64(const double* u0, int64_t n, double dx, double dt, double alpha, int bc,
-                            int64_t nsteps, const double* gT, double* g_u0, double* g_alpha) {
+                            int64_t nsteps, const double* gT, double* g_u0, double* g_alpha, double* g_alpha_abs) {
   if (!u0 || !gT || !g_u0 || !g_alpha || n < 3 || nsteps < 0 || (bc != OR_BC_PERIODIC && bc != OR_BC_MIRROR))
     return -1;
   const double fo_d = (alpha * dt) / (dx * dx);
@@ -211,18 +226,21 @@ int oracle_heat_adjoint_f64(const double* u0, int64_t n, double dx, double dt, d
   memcpy(tape, u0, (size_t)n * sizeof(double));
   for (int64_t m = 0; m < nsteps; ++m) heat_step_f64(tape + m * n, tape + (m + 1) * n, n, fo, c1, bc, 1);
   memcpy(lam, gT, (size_t)n * sizeof(double));
-  long double acc = 0.0L;
+  long double acc = 0.0L, acc_abs = 0.0L;
   for (int64_t m = nsteps - 1; m >= 0; --m) {
     const double* T = tape + m * n;
     for (int64_t i = 0; i < n; ++i) {
-      const double s = T[nb_index(i + 1, n, bc, NULL)] + T[nb_index(i - 1, n, bc, NULL)];
-      acc += (long double)lam[i] * (long double)kk * ((long double)s - 2.0L * (long double)T[i]);
+      const long double tp = (long double)T[nb_index(i + 1, n, bc, NULL)];
+      const long double tm = (long double)T[nb_index(i - 1, n, bc, NULL)];
+      acc += (long double)lam[i] * (long double)kk * ((tp + tm) - 2.0L * (long double)T[i]);
+      acc_abs += fabsl((long double)lam[i]) * (long double)kk * (fabsl(tp) + fabsl(tm) + 2.0L * fabsl((long double)T[i]));
     }
     heat_step_f64(lam, nxt, n, fo, c1, bc, 1);
     memcpy(lam, nxt, (size_t)n * sizeof(double));
   }
   memcpy(g_u0, lam, (size_t)n * sizeof(double));
   *g_alpha = (double)acc;
+  if (g_alpha_abs) *g_alpha_abs = (double)acc_abs;
   free(tape); free(lam); free(nxt);
   return 0;
 }

@@ -7,6 +7,9 @@
 #include <new>
 #include <string>
 
+#include <algorithm>
+
+#include "kernels.cuh"
 #include "runtime.h"
 #include "swept_phases.cuh"
 
@@ -175,6 +178,136 @@ cudaError_t issue_classic(swept_handle* h, void* u, int64_t k0, int64_t k1, cuda
   return cudaSuccess;
 }
 
+// ---------------------------------------------------------------------------
+// adjoint support: checkpoint layout, tape-recording forward, adjoint sweep
+// ---------------------------------------------------------------------------
+struct AdjPlan {
+  int64_t K = 0, nseg = 0;
+  size_t off_ck = 0, off_tape = 0, off_lam = 0, off_w = 0, off_slots = 0, bytes = 0;
+};
+
+AdjPlan adj_layout(const swept_handle* h, int64_t nsteps, int64_t K) {
+  AdjPlan a;
+  const size_t slot = align_up((size_t)h->g.N * h->g.C * sizeof(double));
+  a.K = K;
+  a.nseg = (nsteps + K - 1) / K;
+  a.off_ck = 0;
+  a.off_tape = a.off_ck + (size_t)a.nseg * slot;
+  // the tape's tiers are contiguous runs of N*C values (the kernels index them so)
+  a.off_lam = a.off_tape + align_up((size_t)(h->g.S * K + 1) * h->g.N * h->g.C * sizeof(double));
+  a.off_w = a.off_lam + slot;
+  a.off_slots = a.off_w + slot;
+  a.bytes = a.off_slots + align_up((size_t)2 * h->g.nt * sizeof(double));  // (hi, lo) per block
+  return a;
+}
+
+// steps per segment: whole passes (h/S steps) or the whole run; for a size
+// query (bytes == 0) about sqrt(nsteps * h/S), else the largest that fits
+int64_t adj_segment(const swept_handle* h, int64_t nsteps, size_t bytes) {
+  const int64_t K0 = h->g.h / h->g.S;
+  if (nsteps <= K0) return nsteps;
+  if (bytes == 0) {
+    int64_t m = 1;
+    while ((m + 1) * (m + 1) * K0 <= nsteps) ++m;
+    return std::min<int64_t>(nsteps, m * K0);
+  }
+  if (adj_layout(h, nsteps, nsteps).bytes <= bytes) return nsteps;
+  for (int64_t K = (nsteps / K0) * K0; K >= K0; K -= K0)
+    if (adj_layout(h, nsteps, K).bytes <= bytes) return K;
+  return 0;
+}
+
+int64_t launch_base(const Geom& g, int64_t n_sub, int kind, int64_t pass) {
+  const int64_t q = n_sub / g.h;
+  return pass >= 0 ? (kind == 0 ? 0 : (pass - 1) * (int64_t)g.h) : q * (int64_t)g.h;
+}
+
+size_t adj_smem(const swept_handle* h) { return std::max<size_t>(h->smem, 64 * sizeof(double)); }
+
+// swept forward over n_sub sub-timesteps of u, recording tier L (1..n_sub) into
+// tape slot L (N*C values per slot, slot 0 = the starting state, copied by the caller)
+cudaError_t issue_swept_tape(swept_handle* h, void* u, int64_t n_sub, void* tape, cudaStream_t s) {
+  const Geom& g = h->g;
+  const SchemeImpl* im = h->impl;
+  void* eb[2] = {h->ws + h->off_e0, h->ws + h->off_e1};
+  cudaError_t err = cudaSuccess;
+  swept::for_each_launch(g, n_sub, [&](int kind, int odd, int mode, int hh, int64_t pass) {
+    if (err != cudaSuccess) return;
+    const int64_t base = launch_base(g, n_sub, kind, pass);
+    if (kind == 0) {
+      const int out = pass >= 0 ? (int)(pass & 1) : 0;
+      err = im->up_tape(g, h->k, u, u, eb[out], hh, mode == swept::MODE_GAP, h->threads, h->smem, tape, 0,
+                        n_sub + 1, base, s);
+    } else {
+      const int in = pass >= 1 ? (int)((pass - 1) & 1) : 0;
+      const int out = pass >= 1 ? (int)(pass & 1) : 1;
+      err = im->diamond_tape(g, h->k, u, eb[in], eb[out], odd, mode, hh, h->threads, h->smem, tape, 0, n_sub + 1,
+                             base, s);
+    }
+  });
+  return err;
+}
+
+// adjoint sweep of lam over n_sub reverse sub-timesteps against tape slots n_sub..0
+cudaError_t issue_adjoint(swept_handle* h, const void* ka, void* lam, int64_t n_sub, const void* tape, double* slots,
+                          cudaStream_t s) {
+  const Geom& g = h->g;
+  const SchemeImpl* im = h->impl;
+  void* eb[2] = {h->ws + h->off_e0, h->ws + h->off_e1};
+  const size_t sm = adj_smem(h);
+  cudaError_t err = cudaSuccess;
+  swept::for_each_launch(g, n_sub, [&](int kind, int odd, int mode, int hh, int64_t pass) {
+    if (err != cudaSuccess) return;
+    const int64_t base = launch_base(g, n_sub, kind, pass);
+    if (kind == 0) {
+      const int out = pass >= 0 ? (int)(pass & 1) : 0;
+      err = im->adj_up(g, ka, lam, lam, eb[out], hh, mode == swept::MODE_GAP, h->threads, sm, tape, n_sub, base,
+                       slots, s);
+    } else {
+      const int in = pass >= 1 ? (int)((pass - 1) & 1) : 0;
+      const int out = pass >= 1 ? (int)(pass & 1) : 1;
+      err = im->adj_diamond(g, ka, lam, eb[in], eb[out], odd, mode, hh, h->threads, sm, tape, n_sub, base, slots, s);
+    }
+  });
+  return err;
+}
+
+swept_status adj_check(swept_handle* h, int64_t nsteps, void* ckpt, size_t bytes, AdjPlan* plan) {
+  if (!h->impl->adj_up || h->cfg.dtype != SWEPT_F64)
+    return fail(h, SWEPT_EUNSUPPORTED, "the adjoint exists for heat and KS in FP64 only");
+  if (!ckpt || nsteps < 0 || ((uintptr_t)ckpt % kAlign) != 0)
+    return fail(h, SWEPT_EINVAL, "ckpt_dev NULL or not 256-byte aligned, or nsteps < 0");
+  const int64_t K = adj_segment(h, nsteps, bytes);
+  if (nsteps > 0 && K <= 0) return fail(h, SWEPT_ENOMEM_WORKSPACE, "ckpt_bytes too small for one pass per segment");
+  *plan = adj_layout(h, nsteps, nsteps > 0 ? K : 1);
+  if (plan->bytes > bytes) return fail(h, SWEPT_ENOMEM_WORKSPACE, "ckpt_bytes too small");
+  return SWEPT_OK;
+}
+
+swept_status forward_ckpt(swept_handle* h, void* u, int64_t nsteps, char* ck, size_t bytes, const AdjPlan& a,
+                          cudaStream_t s) {
+  const int64_t NC = h->g.N * h->g.C;
+  const size_t slot = align_up((size_t)NC * sizeof(double));
+  for (int64_t sg = 0; sg < a.nseg; ++sg) {
+    const int64_t Ks = std::min(a.K, nsteps - sg * a.K);
+    cudaError_t e = h->impl->copy(NC, u, ck + a.off_ck + (size_t)sg * slot, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "checkpoint copy");
+    if (sg + 1 < a.nseg) {
+      swept_status st = swept_step_n(h, u, Ks, s);
+      if (st != SWEPT_OK) return st;
+    } else {
+      e = h->impl->copy(NC, u, ck + a.off_tape, s);
+      if (e == cudaSuccess) e = issue_swept_tape(h, u, Ks * h->g.S, ck + a.off_tape, s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "tape-recording forward");
+    }
+  }
+  h->fwd_ckpt = ck;
+  h->fwd_nsteps = nsteps;
+  h->fwd_bytes = bytes;
+  h->fwd_tape_valid = true;
+  return SWEPT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -341,15 +474,73 @@ swept_status swept_run_host(swept_handle* h, const void* u_host_in, void* u_host
 }
 
 swept_status swept_adjoint_ckpt_size(const swept_handle* h, int64_t nsteps, size_t* bytes) {
-  (void)h; (void)nsteps; (void)bytes;
-  return SWEPT_EUNSUPPORTED;
+  if (!h || !bytes || nsteps < 0) return SWEPT_EINVAL;
+  if (!h->impl->adj_up || h->cfg.dtype != SWEPT_F64) return SWEPT_EUNSUPPORTED;
+  *bytes = adj_layout(h, nsteps, std::max<int64_t>(1, adj_segment(h, nsteps, 0))).bytes;
+  return SWEPT_OK;
+}
+
+swept_status swept_forward_ckpt(swept_handle* h, void* u_dev, int64_t nsteps, void* ckpt_dev, size_t ckpt_bytes,
+                                void* stream) {
+  swept_status st = check_ready(h, u_dev, nsteps);
+  if (st != SWEPT_OK) return st;
+  AdjPlan a;
+  st = adj_check(h, nsteps, ckpt_dev, ckpt_bytes, &a);
+  if (st != SWEPT_OK || nsteps == 0) return st;
+  return forward_ckpt(h, u_dev, nsteps, (char*)ckpt_dev, ckpt_bytes, a, (cudaStream_t)stream);
 }
 
 swept_status swept_adjoint(swept_handle* h, const void* u0_dev, const void* gT_dev, int64_t nsteps, void* g_u0_dev,
                            void* g_param_dev, void* ckpt_dev, size_t ckpt_bytes, void* stream) {
-  (void)u0_dev; (void)gT_dev; (void)nsteps; (void)g_u0_dev; (void)g_param_dev; (void)ckpt_dev; (void)ckpt_bytes;
-  (void)stream;
-  return fail(h, SWEPT_EUNSUPPORTED, "adjoint not available in this build");
+  swept_status st = check_ready(h, g_u0_dev, nsteps);
+  if (st != SWEPT_OK) return st;
+  if (!gT_dev || !g_param_dev) return fail(h, SWEPT_EINVAL, "gT_dev or g_param_dev is NULL");
+  AdjPlan a;
+  st = adj_check(h, nsteps, ckpt_dev, ckpt_bytes, &a);
+  if (st != SWEPT_OK) return st;
+  const cudaStream_t s = (cudaStream_t)stream;
+  char* ck = (char*)ckpt_dev;
+  const int64_t NC = h->g.N * h->g.C;
+  const size_t slot = align_up((size_t)NC * sizeof(double));
+  void* lam = ck + a.off_lam;
+  void* w = ck + a.off_w;
+  double* slots = (double*)(ck + a.off_slots);
+  cudaError_t e;
+  if (u0_dev) {
+    e = h->impl->copy(NC, u0_dev, w, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "copy u0");
+    if (nsteps > 0) {
+      st = forward_ckpt(h, w, nsteps, ck, ckpt_bytes, a, s);
+      if (st != SWEPT_OK) return st;
+    }
+  } else if (nsteps > 0 && !(h->fwd_ckpt == ckpt_dev && h->fwd_nsteps == nsteps && h->fwd_bytes == ckpt_bytes)) {
+    return fail(h, SWEPT_EINVAL, "u0_dev is NULL but no swept_forward_ckpt with this ckpt_dev/nsteps/ckpt_bytes");
+  }
+  unsigned char ka[swept::KBYTES];
+  h->impl->make_adj_consts(h->cfg.param, h->cfg.dx, h->cfg.dt, ka);
+  const size_t sm = adj_smem(h);
+  if (sm > 48 * 1024) {
+    e = h->impl->adj_prepare(sm);
+    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint shared-memory limit");
+  }
+  e = cudaMemsetAsync(slots, 0, (size_t)2 * h->g.nt * sizeof(double), s);
+  if (e == cudaSuccess) e = h->impl->copy(NC, gT_dev, lam, s);
+  for (int64_t sg = a.nseg - 1; sg >= 0 && e == cudaSuccess && nsteps > 0; --sg) {
+    const int64_t Ks = std::min(a.K, nsteps - sg * a.K);
+    if (!(sg == a.nseg - 1 && h->fwd_tape_valid)) {
+      e = h->impl->copy(NC, ck + a.off_ck + (size_t)sg * slot, ck + a.off_tape, s);
+      if (e == cudaSuccess) e = h->impl->copy(NC, ck + a.off_ck + (size_t)sg * slot, w, s);
+      if (e == cudaSuccess) e = issue_swept_tape(h, w, Ks * h->g.S, ck + a.off_tape, s);
+    }
+    if (e == cudaSuccess) e = issue_adjoint(h, ka, lam, Ks * h->g.S, ck + a.off_tape, slots, s);
+  }
+  if (a.nseg > 1) h->fwd_tape_valid = false;  // the tape now holds the first segment
+  if (e == cudaSuccess) e = h->impl->copy(NC, lam, g_u0_dev, s);
+  if (e == cudaSuccess) {
+    swept::k_sum_slots<<<1, 32, 0, s>>>(slots, h->g.nt, (double*)g_param_dev);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? SWEPT_OK : cuda_fail(h, e, "swept_adjoint");
 }
 
 swept_status swept_profile_passes(swept_handle* h, void* u_dev, int64_t nsteps, void* stream, double* out_ms,

@@ -27,6 +27,23 @@ struct SchemeImpl {
   // one classic sub-timestep (stage 0 or 1) from `in` into `out`
   cudaError_t (*classic)(const Geom& g, const void* k, int stage, const void* in, void* out, cudaStream_t s);
   cudaError_t (*copy)(int64_t n, const void* src, void* dst, cudaStream_t s);
+  // forward passes that also record every tier into a tape (adjoint support;
+  // nullptr for schemes without an adjoint)
+  cudaError_t (*up_tape)(const Geom& g, const void* k, const void* u_in, void* u_out, void* e_out, int hh,
+                         int write_top, int threads, size_t smem, void* tape, int64_t tier0, int64_t ntiers,
+                         int64_t base, cudaStream_t s);
+  cudaError_t (*diamond_tape)(const Geom& g, const void* k, void* u_out, const void* e_in, void* e_out, int odd,
+                              int mode, int hh, int threads, size_t smem, void* tape, int64_t tier0, int64_t ntiers,
+                              int64_t base, cudaStream_t s);
+  // adjoint constants and passes (FP64 only; nullptr where there is no adjoint)
+  void (*make_adj_consts)(const double* param, double dx, double dt, void* kbuf);
+  cudaError_t (*adj_prepare)(size_t bytes);
+  cudaError_t (*adj_up)(const Geom& g, const void* ka, const void* lam_in, void* lam_out, void* e_out, int hh,
+                        int write_top, int threads, size_t smem, const void* tape, int64_t top, int64_t base,
+                        double* slots, cudaStream_t s);
+  cudaError_t (*adj_diamond)(const Geom& g, const void* ka, void* lam_out, const void* e_in, void* e_out, int odd,
+                             int mode, int hh, int threads, size_t smem, const void* tape, int64_t top, int64_t base,
+                             double* slots, cudaStream_t s);
 };
 
 const SchemeImpl* heat_impl(int dtype);

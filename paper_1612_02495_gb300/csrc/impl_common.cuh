@@ -45,6 +45,72 @@ struct Launch {
     k_copy<T><<<1024, 256, 0, s>>>(n, (const T*)src, (T*)dst);
     return cudaGetLastError();
   }
+  static Tape<T> mk_tape(void* tape, int64_t tier0, int64_t ntiers, int64_t base) {
+    Tape<T> t;
+    t.p = (T*)tape;
+    t.tier0 = tier0;
+    t.ntiers = ntiers;
+    t.base = base;
+    return t;
+  }
+  static cudaError_t prepare_tape(size_t bytes) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_swept_up_tape<T, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_swept_diamond_tape<T, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bytes);
+  }
+  static cudaError_t up_tape(const Geom& g, const void* k, const void* u_in, void* u_out, void* e_out, int hh,
+                             int write_top, int threads, size_t smem, void* tape, int64_t tier0, int64_t ntiers,
+                             int64_t base, cudaStream_t s) {
+    if (smem > 48 * 1024) {
+      cudaError_t e = prepare_tape(smem);
+      if (e != cudaSuccess) return e;
+    }
+    k_swept_up_tape<T, Op><<<(unsigned)g.nt, threads, smem, s>>>(g, kc(k), (const T*)u_in, (T*)u_out, (T*)e_out, hh,
+                                                                 write_top, mk_tape(tape, tier0, ntiers, base));
+    return cudaGetLastError();
+  }
+  static cudaError_t diamond_tape(const Geom& g, const void* k, void* u_out, const void* e_in, void* e_out, int odd,
+                                  int mode, int hh, int threads, size_t smem, void* tape, int64_t tier0,
+                                  int64_t ntiers, int64_t base, cudaStream_t s) {
+    if (smem > 48 * 1024) {
+      cudaError_t e = prepare_tape(smem);
+      if (e != cudaSuccess) return e;
+    }
+    k_swept_diamond_tape<T, Op><<<(unsigned)g.nt, threads, smem, s>>>(
+        g, kc(k), (T*)u_out, (const T*)e_in, (T*)e_out, odd, mode, hh, mk_tape(tape, tier0, ntiers, base));
+    return cudaGetLastError();
+  }
+};
+
+// launch wrappers of the adjoint passes for adjoint operator AOp
+template <typename T, class AOp>
+struct AdjLaunch {
+  static typename AOp::K kc(const void* k) {
+    typename AOp::K kk;
+    memcpy(&kk, k, sizeof(kk));
+    return kk;
+  }
+  static cudaError_t prepare(size_t bytes) {
+    cudaError_t e = cudaFuncSetAttribute(k_adj_up<T, AOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_adj_diamond<T, AOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  }
+  static cudaError_t up(const Geom& g, const void* ka, const void* lam_in, void* lam_out, void* e_out, int hh,
+                        int write_top, int threads, size_t smem, const void* tape, int64_t top, int64_t base,
+                        double* slots, cudaStream_t s) {
+    k_adj_up<T, AOp><<<(unsigned)g.nt, threads, smem, s>>>(g, kc(ka), (const T*)lam_in, (T*)lam_out, (T*)e_out, hh,
+                                                           write_top, (const T*)tape, top, base, slots);
+    return cudaGetLastError();
+  }
+  static cudaError_t diamond(const Geom& g, const void* ka, void* lam_out, const void* e_in, void* e_out, int odd,
+                             int mode, int hh, int threads, size_t smem, const void* tape, int64_t top, int64_t base,
+                             double* slots, cudaStream_t s) {
+    k_adj_diamond<T, AOp><<<(unsigned)g.nt, threads, smem, s>>>(g, kc(ka), (T*)lam_out, (const T*)e_in, (T*)e_out,
+                                                                odd, mode, hh, (const T*)tape, top, base, slots);
+    return cudaGetLastError();
+  }
 };
 
 }  // namespace swept

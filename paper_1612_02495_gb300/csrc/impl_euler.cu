@@ -31,8 +31,9 @@ cudaError_t euler_classic(const Geom& g, const void* kb, int stage, const void* 
 template <typename T>
 SchemeImpl make_euler() {
   using L = Launch<T, EulerOp<T>>;
-  return SchemeImpl{2, 2, 3, (int)sizeof(T), euler_consts<T>, L::smem_values, L::prepare, L::up, L::diamond,
-                    euler_classic<T>, L::copy};
+  SchemeImpl im{2, 2, 3, (int)sizeof(T), euler_consts<T>, L::smem_values, L::prepare, L::up, L::diamond,
+                euler_classic<T>, L::copy, L::up_tape, L::diamond_tape, nullptr, nullptr, nullptr, nullptr};
+  return im;
 }
 
 const SchemeImpl kEulerF32 = make_euler<float>();

@@ -14,15 +14,36 @@ void heat_consts(const double* param, double dx, double dt, void* kbuf) {
   memcpy(kbuf, &k, sizeof(k));
 }
 
+// adjoint: Fo, 1 - 2 Fo and dt / dx^2 (the derivative of Fo with respect to alpha)
+void heat_adj_consts(const double* param, double dx, double dt, void* kbuf) {
+  HeatAdjOp<double>::K k;
+  const double fo = (param[0] * dt) / (dx * dx);
+  k.fo = fo;
+  k.c1 = 1.0 - 2.0 * fo;
+  k.kk = dt / (dx * dx);
+  memcpy(kbuf, &k, sizeof(k));
+}
+
 template <typename T>
 SchemeImpl make_heat() {
   using L = Launch<T, HeatOp<T>>;
-  return SchemeImpl{1, 1, 1, (int)sizeof(T), heat_consts<T>, L::smem_values, L::prepare, L::up, L::diamond,
-                    L::classic, L::copy};
+  SchemeImpl im{1, 1, 1, (int)sizeof(T), heat_consts<T>, L::smem_values, L::prepare, L::up, L::diamond,
+                L::classic, L::copy, L::up_tape, L::diamond_tape, nullptr, nullptr, nullptr, nullptr};
+  return im;
+}
+
+SchemeImpl make_heat_f64() {
+  using A = AdjLaunch<double, HeatAdjOp<double>>;
+  SchemeImpl im = make_heat<double>();
+  im.make_adj_consts = heat_adj_consts;
+  im.adj_prepare = A::prepare;
+  im.adj_up = A::up;
+  im.adj_diamond = A::diamond;
+  return im;
 }
 
 const SchemeImpl kHeatF32 = make_heat<float>();
-const SchemeImpl kHeatF64 = make_heat<double>();
+const SchemeImpl kHeatF64 = make_heat_f64();
 
 }  // namespace
 

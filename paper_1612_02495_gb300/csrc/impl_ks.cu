@@ -17,15 +17,41 @@ void ks_consts(const double* param, double dx, double dt, void* kbuf) {
   memcpy(kbuf, &k, sizeof(k));
 }
 
+// adjoint: 2 c_a, c_2, c_4, -dt, -dt/2, and -dt k4, -(dt/2) k4 with k4 = 1/dx^4 = dc_4/dnu
+void ks_adj_consts(const double* param, double dx, double dt, void* kbuf) {
+  KsAdjOp<double>::K k;
+  const double idx2 = 1.0 / (dx * dx);
+  const double k4 = idx2 * idx2;
+  k.ca2 = 2.0 * (1.0 / (4.0 * dx));
+  k.c2 = idx2;
+  k.c4 = param[0] * k4;
+  k.mdt = -dt;
+  k.mdth = -0.5 * dt;
+  k.mdtk4 = -dt * k4;
+  k.mdthk4 = -0.5 * dt * k4;
+  memcpy(kbuf, &k, sizeof(k));
+}
+
 template <typename T>
 SchemeImpl make_ks() {
   using L = Launch<T, KsOp<T>>;
-  return SchemeImpl{2, 2, 1, (int)sizeof(T), ks_consts<T>, L::smem_values, L::prepare, L::up, L::diamond,
-                    L::classic, L::copy};
+  SchemeImpl im{2, 2, 1, (int)sizeof(T), ks_consts<T>, L::smem_values, L::prepare, L::up, L::diamond,
+                L::classic, L::copy, L::up_tape, L::diamond_tape, nullptr, nullptr, nullptr, nullptr};
+  return im;
+}
+
+SchemeImpl make_ks_f64() {
+  using A = AdjLaunch<double, KsAdjOp<double>>;
+  SchemeImpl im = make_ks<double>();
+  im.make_adj_consts = ks_adj_consts;
+  im.adj_prepare = A::prepare;
+  im.adj_up = A::up;
+  im.adj_diamond = A::diamond;
+  return im;
 }
 
 const SchemeImpl kKsF32 = make_ks<float>();
-const SchemeImpl kKsF64 = make_ks<double>();
+const SchemeImpl kKsF64 = make_ks_f64();
 
 }  // namespace
 

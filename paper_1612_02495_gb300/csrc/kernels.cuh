@@ -147,7 +147,19 @@ struct LevelImpl<T, EulerOp<T>> {
 // ---------------------------------------------------------------------------
 // device execution context for the pass phases (swept_phases.cuh)
 // ---------------------------------------------------------------------------
-template <typename T, class Op>
+// Tape: every value a pass computes at absolute tier L is also stored at
+// tape[(L - tier0) * C * N + c * N + x] when 0 <= L - tier0 < ntiers (used to
+// record the forward tiers the adjoint reads).  `base` is the absolute tier
+// of the launch's local tier 0.
+template <typename T>
+struct Tape {
+  T* p = nullptr;
+  int64_t tier0 = 0;
+  int64_t ntiers = 0;
+  int64_t base = 0;
+};
+
+template <typename T, class Op, bool TAPE = false>
 struct DevCtx {
   T* sm;
   Geom g;
@@ -156,6 +168,7 @@ struct DevCtx {
   T* u_out;
   const T* __restrict__ e_in;
   T* __restrict__ e_out;
+  Tape<T> tape;
 
   template <class F>
   __device__ __forceinline__ void for_range(int lo, int hi, F&& f) {
@@ -171,8 +184,18 @@ struct DevCtx {
   }
   __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) { row(r, c)[j] = e_in[e]; }
   __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) { e_out[e] = row(r, c)[j]; }
-  __device__ __forceinline__ void level(int s, int /*base*/, int lo, int hi, int64_t /*origin*/, int wall) {
+  __device__ __forceinline__ void level(int s, int base, int lo, int hi, int64_t origin, int wall) {
     LevelImpl<T, Op>::run(sm, g.M, stage_of(g, s), s & 1, lo, hi, wall, k);
+    if (TAPE) {
+      // each thread stores the values it computed itself, so no barrier is needed first
+      const int64_t slot = tape.base + base + s - tape.tier0;
+      if (slot >= 0 && slot < tape.ntiers)
+        for (int j = lo + (int)threadIdx.x; j < hi; j += (int)blockDim.x) {
+          const int64_t x = wrap_n(origin + j, g.N);
+#pragma unroll
+          for (int c = 0; c < Op::C; ++c) tape.p[(slot * Op::C + c) * g.N + x] = row(s & 1, c)[j];
+        }
+    }
     __syncthreads();
   }
 };
@@ -181,7 +204,7 @@ template <typename T, class Op>
 __global__ void __launch_bounds__(1024) k_swept_up(Geom g, typename Op::K k, const T* u_in, T* u_out, T* e_out,
                                                    int hh, int write_top) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  DevCtx<T, Op> cx{reinterpret_cast<T*>(smraw), g, k, u_in, u_out, nullptr, e_out};
+  DevCtx<T, Op> cx{reinterpret_cast<T*>(smraw), g, k, u_in, u_out, nullptr, e_out, Tape<T>{}};
   run_up(cx, g, (int64_t)blockIdx.x, hh, write_top != 0);
 }
 
@@ -189,8 +212,162 @@ template <typename T, class Op>
 __global__ void __launch_bounds__(1024) k_swept_diamond(Geom g, typename Op::K k, T* u_out, const T* e_in, T* e_out,
                                                         int odd, int mode, int hh) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  DevCtx<T, Op> cx{reinterpret_cast<T*>(smraw), g, k, nullptr, u_out, e_in, e_out};
+  DevCtx<T, Op> cx{reinterpret_cast<T*>(smraw), g, k, nullptr, u_out, e_in, e_out, Tape<T>{}};
   run_diamond(cx, g, (int64_t)blockIdx.x, odd, mode, hh);
+}
+
+// forward passes that also record every computed tier into a tape
+template <typename T, class Op>
+__global__ void __launch_bounds__(1024) k_swept_up_tape(Geom g, typename Op::K k, const T* u_in, T* u_out, T* e_out,
+                                                        int hh, int write_top, Tape<T> tape) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  DevCtx<T, Op, true> cx{reinterpret_cast<T*>(smraw), g, k, u_in, u_out, nullptr, e_out, tape};
+  run_up(cx, g, (int64_t)blockIdx.x, hh, write_top != 0);
+}
+
+template <typename T, class Op>
+__global__ void __launch_bounds__(1024) k_swept_diamond_tape(Geom g, typename Op::K k, T* u_out, const T* e_in,
+                                                             T* e_out, int odd, int mode, int hh, Tape<T> tape) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  DevCtx<T, Op, true> cx{reinterpret_cast<T*>(smraw), g, k, nullptr, u_out, e_in, e_out, tape};
+  run_diamond(cx, g, (int64_t)blockIdx.x, odd, mode, hh);
+}
+
+// ---------------------------------------------------------------------------
+// adjoint passes: the same swept schedule on lam, reverse tier L reading the
+// forward state of tape slot (S K - L) at the same point, and accumulating the
+// parameter derivative per thread; each block adds its sum to slot[block]
+// (blocks of later launches add to the same slot in launch order, so the
+// result is deterministic).
+// ---------------------------------------------------------------------------
+template <typename T, class AOp>
+__device__ __forceinline__ void adjoint_level(T* sm, int M, int stage, int out_row, int lo, int hi, int wall,
+                                              int64_t origin, int64_t N, const T* fwd, const typename AOp::K& k,
+                                              KahanAcc& acc) {
+  constexpr int R = AOp::R;
+  const T* in = sm + (out_row ^ 1) * M;
+  T* out = sm + out_row * M;
+  for (int j = lo + (int)threadIdx.x; j < hi; j += (int)blockDim.x) {
+    T v[2 * R + 1];
+#pragma unroll
+    for (int d = 0; d <= 2 * R; ++d) v[d] = in[nbr(j, d - R, wall)];
+    const T w = fwd[wrap_n(origin + j, N)];
+    if (stage == 0)
+      out[j] = AOp::template point<0>(v, T(0), w, k, acc);
+    else
+      out[j] = AOp::template point<1>(v, out[j], w, k, acc);
+  }
+}
+
+template <typename T, class AOp>
+struct AdjCtx {
+  T* sm;
+  Geom g;
+  typename AOp::K k;
+  const T* u_in;
+  T* u_out;
+  const T* __restrict__ e_in;
+  T* __restrict__ e_out;
+  const T* __restrict__ tape;  // forward tiers 0 .. S K of the segment, N values each
+  int64_t top;                 // S K: reverse tier L reads forward slot top - L
+  int64_t base;                // absolute reverse tier of the launch's local tier 0
+  KahanAcc acc;
+
+  template <class F>
+  __device__ __forceinline__ void for_range(int lo, int hi, F&& f) {
+    for (int i = lo + (int)threadIdx.x; i < hi; i += (int)blockDim.x) f(i);
+  }
+  __device__ __forceinline__ void sync() { __syncthreads(); }
+  __device__ __forceinline__ T* row(int r, int c) { return sm + (r * AOp::C + c) * g.M; }
+  __device__ __forceinline__ void load_u(int r, int c, int j, int64_t x) {
+    row(r, c)[j] = u_in[c * g.N + wrap_n(x, g.N)];
+  }
+  __device__ __forceinline__ void store_u(int r, int c, int j, int64_t x) {
+    u_out[c * g.N + wrap_n(x, g.N)] = row(r, c)[j];
+  }
+  __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) { row(r, c)[j] = e_in[e]; }
+  __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) { e_out[e] = row(r, c)[j]; }
+  __device__ __forceinline__ void level(int s, int b, int lo, int hi, int64_t origin, int wall) {
+    const int64_t L = base + b + s;
+    adjoint_level<T, AOp>(sm, g.M, stage_of(g, s), s & 1, lo, hi, wall, origin, g.N, tape + (top - L) * g.N, k,
+                          acc);
+    __syncthreads();
+  }
+};
+
+// double-double arithmetic for the parameter-derivative reduction
+struct DD {
+  double hi, lo;
+};
+__device__ __forceinline__ DD two_sum(double a, double b) {
+  const double s = __dadd_rn(a, b);
+  const double bp = __dsub_rn(s, a);
+  const double e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bp)), __dsub_rn(b, bp));
+  return DD{s, e};
+}
+__device__ __forceinline__ DD dd_add(DD a, DD b) {
+  const DD s = two_sum(a.hi, b.hi);
+  return two_sum(s.hi, __dadd_rn(s.lo, __dadd_rn(a.lo, b.lo)));
+}
+
+// deterministic block sum of one double-double per thread (blockDim.x a
+// multiple of 32); the result is valid in thread 0
+__device__ __forceinline__ DD block_sum(DD v, double* scratch) {
+  for (int o = 16; o > 0; o >>= 1) {
+    DD w;
+    w.hi = __shfl_down_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
+    v = dd_add(v, w);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    scratch[2 * warp] = v.hi;
+    scratch[2 * warp + 1] = v.lo;
+  }
+  __syncthreads();
+  DD t{0.0, 0.0};
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = dd_add(t, DD{scratch[2 * w], scratch[2 * w + 1]});
+  return t;
+}
+
+// slots hold one double-double (hi, lo) per block
+__device__ __forceinline__ void add_to_slot(double* slots, DD t) {
+  const DD r = dd_add(DD{slots[2 * blockIdx.x], slots[2 * blockIdx.x + 1]}, t);
+  slots[2 * blockIdx.x] = r.hi;
+  slots[2 * blockIdx.x + 1] = r.lo;
+}
+
+template <typename T, class AOp>
+__global__ void __launch_bounds__(1024) k_adj_up(Geom g, typename AOp::K k, const T* u_in, T* u_out, T* e_out, int hh,
+                                                 int write_top, const T* tape, int64_t top, int64_t base,
+                                                 double* slots) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  AdjCtx<T, AOp> cx{reinterpret_cast<T*>(smraw), g, k, u_in, u_out, nullptr, e_out, tape, top, base, KahanAcc{}};
+  run_up(cx, g, (int64_t)blockIdx.x, hh, write_top != 0);
+  const DD t = block_sum(DD{cx.acc.s, -cx.acc.c}, reinterpret_cast<double*>(smraw));
+  if (threadIdx.x == 0) add_to_slot(slots, t);
+}
+
+template <typename T, class AOp>
+__global__ void __launch_bounds__(1024) k_adj_diamond(Geom g, typename AOp::K k, T* u_out, const T* e_in, T* e_out,
+                                                      int odd, int mode, int hh, const T* tape, int64_t top,
+                                                      int64_t base, double* slots) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  AdjCtx<T, AOp> cx{reinterpret_cast<T*>(smraw), g, k, nullptr, u_out, e_in, e_out, tape, top, base, KahanAcc{}};
+  run_diamond(cx, g, (int64_t)blockIdx.x, odd, mode, hh);
+  const DD t = block_sum(DD{cx.acc.s, -cx.acc.c}, reinterpret_cast<double*>(smraw));
+  if (threadIdx.x == 0) add_to_slot(slots, t);
+}
+
+// out[0] = double-double sum of the n (hi, lo) slots in index order (one thread: deterministic)
+static __global__ void k_sum_slots(const double* slots, int64_t n, double* out) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    DD t{0.0, 0.0};
+    for (int64_t i = 0; i < n; ++i) t = dd_add(t, DD{slots[2 * i], slots[2 * i + 1]});
+    out[0] = __dadd_rn(t.hi, t.lo);
+  }
 }
 
 // ---------------------------------------------------------------------------

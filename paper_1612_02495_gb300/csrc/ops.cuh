@@ -154,4 +154,79 @@ struct EulerOp {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Discrete adjoints (not in the paper): the exact transposes of the forward
+// operation sequence, run backwards in time as the same two-stage, radius-r
+// stencil, with the forward state of each tier read from a tape.
+//
+// KS, reverse of one step m (lam' = dL/du^{m+1}):
+//   gT(lam; w)_j = fma(c_4, d4, fma(c_2, d2, (2 c_a w_j)(lam_{j-1} - lam_{j+1})))
+//     with sp1, sp2, d2, d4 of lam as in the forward operator
+//   stage 0:  mu  = -dt gT(lam'; P^m)                       (odd reverse tiers)
+//   stage 1:  lam = fma(-dt/2, gT(mu; u^m), lam' + mu)      (even reverse tiers)
+// dL/dnu = sum -dt k4 lam'_j d4(P^m)_j - (dt/2) k4 mu_j d4(u^m)_j, accumulated as
+// the equal sums -dt k4 d4(lam')_j P^m_j and -(dt/2) k4 d4(mu)_j u^m_j (the
+// periodic fourth difference is symmetric), so the d4 already computed in gT
+// is reused.
+// ---------------------------------------------------------------------------
+// Compensated (Kahan) accumulation of the parameter derivative: the error is
+// about 2 eps sum|terms|, independent of the number of terms; the value is
+// the double-double (s, -c).
+struct KahanAcc {
+  double s = 0.0, c = 0.0;
+  __device__ __forceinline__ void add(double x) {
+    const double y = __dsub_rn(x, c);
+    const double t = __dadd_rn(s, y);
+    c = __dsub_rn(__dsub_rn(t, s), y);
+    s = t;
+  }
+};
+
+template <typename T>
+struct KsAdjOp {
+  static constexpr int R = 2, S = 2, C = 1;
+  struct K {
+    T ca2, c2, c4, mdt, mdth, mdtk4, mdthk4;
+  };
+  // v[0..4] = lam_{j-2} .. lam_{j+2}; w = forward state at j; d4 returned for dnu
+  __device__ __forceinline__ static T gT(const T* v, T w, const K& k, T& d4) {
+    const T sp1 = add_rn(v[3], v[1]);
+    const T sp2 = add_rn(v[4], v[0]);
+    const T dl = sub_rn(v[1], v[3]);
+    const T nl = mul_rn(mul_rn(k.ca2, w), dl);
+    const T d2 = fma_rn(T(-2), v[2], sp1);
+    d4 = fma_rn(T(6), v[2], fma_rn(T(-4), sp1, sp2));
+    return fma_rn(k.c4, d4, fma_rn(k.c2, d2, nl));
+  }
+  template <int STAGE>
+  __device__ __forceinline__ static T point(const T* v, T prev2, T w, const K& k, KahanAcc& acc) {
+    T d4;
+    const T g = gT(v, w, k, d4);
+    if (STAGE == 0) {
+      acc.add((double)mul_rn(mul_rn(k.mdtk4, d4), w));
+      return mul_rn(k.mdt, g);
+    }
+    acc.add((double)mul_rn(mul_rn(k.mdthk4, d4), w));
+    return fma_rn(k.mdth, g, add_rn(prev2, v[2]));
+  }
+};
+
+// Heat: FTCS is linear with a symmetric stencil, so the reverse step is the
+// forward update applied to lam:  lam_j = fma(Fo, lam'_{j+1} + lam'_{j-1}, c1 lam'_j).
+// dL/dalpha = sum (dt/dx^2) lam'_j (T_{j+1} + T_{j-1} - 2 T_j)^m, accumulated as
+// the equal sum (dt/dx^2) (lam'_{j+1} + lam'_{j-1} - 2 lam'_j) T^m_j.
+template <typename T>
+struct HeatAdjOp {
+  static constexpr int R = 1, S = 1, C = 1;
+  struct K {
+    T fo, c1, kk;
+  };
+  template <int STAGE>
+  __device__ __forceinline__ static T point(const T* v, T /*prev2*/, T w, const K& k, KahanAcc& acc) {
+    const T s = add_rn(v[2], v[0]);
+    acc.add((double)mul_rn(mul_rn(k.kk, fma_rn(T(-2), v[1], s)), w));
+    return fma_rn(k.fo, s, mul_rn(k.c1, v[1]));
+  }
+};
+
 }  // namespace swept

@@ -28,6 +28,12 @@ struct swept_handle {
   cudaStream_t cap = nullptr;
   std::map<std::string, cudaGraphExec_t> graphs;
   std::string err;
+  // last swept_forward_ckpt: its checkpoints (and the recorded tape of its last
+  // segment) are what swept_adjoint(u0 = NULL) continues from
+  const void* fwd_ckpt = nullptr;
+  int64_t fwd_nsteps = -1;
+  size_t fwd_bytes = 0;
+  bool fwd_tape_valid = false;
 };
 
 namespace swept {

@@ -65,6 +65,7 @@ swept_step_n = _sig("swept_step_n", [_H, _P, _I64, _P])
 classic_step_n = _sig("classic_step_n", [_H, _P, _I64, _P])
 swept_run_host = _sig("swept_run_host", [_H, _P, _P, _P, _I64, _I32, _P])
 swept_adjoint_ckpt_size = _sig("swept_adjoint_ckpt_size", [_H, _I64, ctypes.POINTER(_SZ)])
+swept_forward_ckpt = _sig("swept_forward_ckpt", [_H, _P, _I64, _P, _SZ, _P])
 swept_adjoint = _sig("swept_adjoint", [_H, _P, _P, _I64, _P, _P, _P, _SZ, _P])
 swept_profile_passes = _sig("swept_profile_passes", [_H, _P, _I64, _P, ctypes.POINTER(ctypes.c_double),
                                                      ctypes.POINTER(_I64)])
@@ -191,6 +192,32 @@ class Solver:
         names = ("up", "diamond", "down", "remainder")
         return {names[i]: (ms[i], cnt[i]) for i in range(4)}
 
+    def ckpt_size(self, nsteps):
+        """swept_adjoint_ckpt_size: checkpoint bytes for the default segment length."""
+        sz = _SZ()
+        check(swept_adjoint_ckpt_size(self.h, int(nsteps), ctypes.byref(sz)), self.h, "swept_adjoint_ckpt_size")
+        return int(sz.value)
+
+    def forward_ckpt(self, u, nsteps, ckpt, stream=None):
+        """swept_forward_ckpt: advance u in place and record checkpoints into ckpt (uint8 CUDA tensor)."""
+        self._check_u(u)
+        check(swept_forward_ckpt(self.h, ctypes.c_void_p(u.data_ptr()), int(nsteps), ctypes.c_void_p(ckpt.data_ptr()),
+                                 ckpt.numel(), _stream_ptr(stream)), self.h, "swept_forward_ckpt")
+        return u
+
+    def adjoint(self, gT, nsteps, ckpt, u0=None, g_u0=None, g_param=None, stream=None):
+        """swept_adjoint -> (dL/du0 tensor, dL/dparam 1-element float64 tensor)."""
+        import torch
+
+        self._check_u(gT)
+        g_u0 = torch.empty_like(gT) if g_u0 is None else g_u0
+        g_param = torch.zeros(1, dtype=torch.float64, device=gT.device) if g_param is None else g_param
+        check(swept_adjoint(self.h, ctypes.c_void_p(u0.data_ptr()) if u0 is not None else None,
+                            ctypes.c_void_p(gT.data_ptr()), int(nsteps), ctypes.c_void_p(g_u0.data_ptr()),
+                            ctypes.c_void_p(g_param.data_ptr()), ctypes.c_void_p(ckpt.data_ptr()), ckpt.numel(),
+                            _stream_ptr(stream)), self.h, "swept_adjoint")
+        return g_u0, g_param
+
     def sync_status(self, stream=None):
         check(swept_sync_status(self.h, _stream_ptr(stream)), self.h, "swept_sync_status")
 
@@ -207,3 +234,53 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class SweptSolve:
+    """Differentiable swept solve: u(T) = solve(u0, param) for nsteps steps.
+
+    `SweptSolve.apply(u0, param, nsteps, scheme=KS, bc=BC_PERIODIC, dx=..., dt=..., tile_w=0, ckpt_bytes=0)`
+    returns u(T) (a new tensor).  The backward pass returns dL/du0 and dL/dparam
+    through the library's adjoint (swept_adjoint): KS (param = nu) or heat
+    (param = alpha), FP64.  The forward pass records checkpoints
+    (swept_forward_ckpt); ckpt_bytes = 0 uses swept_adjoint_ckpt_size.
+    """
+
+    @staticmethod
+    def apply(u0, param, nsteps, **kw):
+        return _swept_solve_fn().apply(u0, param, nsteps, kw)
+
+
+_FN = None
+
+
+def _swept_solve_fn():
+    global _FN
+    if _FN is not None:
+        return _FN
+    import torch
+
+    class _Fn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, u0, param, nsteps, kw):
+            scheme = kw.get("scheme", KS)
+            sol = Solver(scheme, F64, u0.shape[-1], kw["dx"], kw["dt"], float(param), bc=kw.get("bc", BC_PERIODIC),
+                         tile_w=kw.get("tile_w", 0), threads=kw.get("threads", 0))
+            nbytes = kw.get("ckpt_bytes", 0) or sol.ckpt_size(nsteps)
+            ckpt = torch.empty(int(nbytes), dtype=torch.uint8, device=u0.device)
+            u = u0.detach().clone().contiguous()
+            sol.forward_ckpt(u, nsteps, ckpt)
+            ctx.sol, ctx.ckpt, ctx.nsteps = sol, ckpt, nsteps
+            ctx.param_shape = param.shape if torch.is_tensor(param) else None
+            ctx.param_device = param.device if torch.is_tensor(param) else None
+            return u
+
+        @staticmethod
+        def backward(ctx, gT):
+            g_u0, g_param = ctx.sol.adjoint(gT.contiguous(), ctx.nsteps, ctx.ckpt)
+            ctx.sol.close()
+            gp = g_param.reshape(ctx.param_shape).to(ctx.param_device) if ctx.param_shape is not None else None
+            return g_u0, gp, None, None
+
+    _FN = _Fn
+    return _FN
