@@ -163,6 +163,51 @@ swept_status swept_forward_ckpt(swept_handle* h, void* u_dev, int64_t nsteps, vo
 swept_status swept_adjoint(swept_handle* h, const void* u0_dev, const void* gT_dev, int64_t nsteps, void* g_u0_dev,
                            void* g_param_dev, void* ckpt_dev, size_t ckpt_bytes, void* stream);
 
+/* ------------------------------------------------------------------------- */
+/* Batched solves (not in the paper): many independent heat / KS problems of   */
+/* different sizes and step counts, all in one dtype, advanced by one          */
+/* persistent kernel launch (captured in a CUDA graph).  Each problem runs the */
+/* same swept launch sequence as swept_step_n (results equal it bit for bit);  */
+/* the passes of all problems form one work queue of (problem, pass, tile)     */
+/* items ordered by pass, whose blocks wait (bounded) for the two tiles they   */
+/* read to finish the previous pass.                                           */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t scheme;  /* SWEPT_HEAT or SWEPT_KS (periodic) */
+  int32_t tile_w;  /* W for this problem, 0 = largest power of two <= 512 giving >= 2 tiles */
+  int64_t n;       /* grid points (a multiple of W, >= 2W) */
+  int64_t nsteps;  /* timesteps */
+  double dx, dt;
+  double param;    /* alpha (heat) or nu (KS) */
+} swept_batch_problem;
+
+typedef struct swept_batch swept_batch;
+
+enum {
+  SWEPT_BATCH_SPIN_LIMIT = 1, /* iterations a block waits for an input tile before SWEPT_ETIMEOUT (default 2^24) */
+  SWEPT_BATCH_START_ITEM = 2, /* first queue item to run (0; larger values leave inputs missing: for fault tests) */
+  SWEPT_BATCH_GRID = 3        /* cap on the persistent grid (0 = all co-resident blocks) */
+};
+
+/* Plan a batch (host only).  threads = block size for every item (0 = 256).
+ * Errors: SWEPT_EINVAL (a problem violates the constraints above). */
+swept_status swept_batch_plan(const swept_batch_problem* problems, int64_t count, int32_t dtype, int32_t threads,
+                              swept_batch** out);
+/* Layout: offsets[count] = first value of each problem's state in the batch
+ * state array (256-byte aligned starts), state_values = its length, ws_bytes =
+ * device workspace size, items = queue length.  Any output may be NULL. */
+swept_status swept_batch_sizes(const swept_batch* b, int64_t* offsets, int64_t* state_values, size_t* ws_bytes,
+                               int64_t* items);
+/* Bind caller-owned workspace (uploads the plan; synchronous). */
+swept_status swept_batch_bind_workspace(swept_batch* b, void* ws_dev, size_t bytes);
+swept_status swept_batch_set_option(swept_batch* b, int32_t option, int64_t value);
+/* Advance every problem of the batch state u_dev by its nsteps, in place. */
+swept_status swept_batch_run(swept_batch* b, void* u_dev, void* stream);
+/* Synchronize `stream`, then return SWEPT_ETIMEOUT if a bounded wait ran out. */
+swept_status swept_batch_sync_status(swept_batch* b, void* stream);
+swept_status swept_batch_last_error(const swept_batch* b, char* buf, size_t len);
+void swept_batch_free(swept_batch* b);
+
 /* Tracing: run swept_step_n's launch sequence for nsteps on `stream` with
  * direct launches (no graph) and a CUDA event pair around every launch, then
  * synchronize.  out_ms[4] receives the summed device time and out_count[4] the

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libswept.so")
 
-SOURCES = ["api.cu", "impl_heat.cu", "impl_ks.cu", "impl_euler.cu", "check.cpp", "noalloc.cu"]
+SOURCES = ["api.cu", "impl_heat.cu", "impl_ks.cu", "impl_euler.cu", "check.cpp", "noalloc.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "--fmad=false", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
           "-I", INCLUDE, "-I", CSRC]

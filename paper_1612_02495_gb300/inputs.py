@@ -14,8 +14,9 @@ Workloads (shapes follow the paper's test problems, Section "Test cases"):
   euler  Sod tube on [0, 1]: (rho, u, p) = (1, 0, 1) for x < 0.5 and
          (0.125, 0, 0.1) after, rho and p each times (1 + 0.01 U(-1, 1)),
          gamma = 1.4, fixed dt = 0.4 dx / 2.5 rounded so that t = 0.2 is hit.
-  batch  problems with N = floor(2^U(10, 18)), heat / KS 50/50,
-         steps ~ U{1000..20000}.
+  batch  problems with N = 2^U(10, 18) rounded to a multiple of 1024 (so every
+         tile width up to 512 divides every problem), heat / KS 50/50,
+         steps ~ U{1000..20000}; per-problem ICs as above, seeded per problem.
 """
 import math
 
@@ -79,10 +80,26 @@ def euler_problem(n=1 << 16, seed=2, dtype=np.float64, gamma=1.4, perturb=0.01):
     return dict(U0=U0.astype(dtype), dx=dx, dt=dt, nsteps=nsteps, gamma=gamma, x=xc)
 
 
-def batch_problems(count=4096, seed=3, log2_lo=10, log2_hi=18, steps_lo=1000, steps_hi=20000):
+def batch_problems(count=4096, seed=3, log2_lo=10, log2_hi=18, steps_lo=1000, steps_hi=20000, quantum=1024):
     """Sizes, scheme kinds (0 heat, 1 KS) and step counts of the batched workload."""
     g = rng(seed)
-    n = np.floor(2.0 ** g.uniform(log2_lo, log2_hi, size=count)).astype(np.int64)
+    raw = 2.0 ** g.uniform(log2_lo, log2_hi, size=count)
+    n = (np.maximum(1, np.rint(raw / quantum)) * quantum).astype(np.int64)
     kind = g.integers(0, 2, size=count)
     steps = g.integers(steps_lo, steps_hi + 1, size=count)
     return dict(n=n, kind=kind, steps=steps)
+
+
+def batch_instances(spec, dtype=np.float64, seed=4):
+    """Per-problem parameters and initial states for a batch_problems() spec:
+    list of dicts (scheme 0 heat / 1 KS, n, nsteps, dx, dt, param, u0)."""
+    out = []
+    for i, (n, kind, steps) in enumerate(zip(spec["n"], spec["kind"], spec["steps"])):
+        n = int(n)
+        if kind == 0:
+            p = heat_problem(n=n, seed=seed * 100003 + i, dtype=dtype)
+            out.append(dict(scheme=0, n=n, nsteps=int(steps), dx=p["dx"], dt=p["dt"], param=p["alpha"], u0=p["u0"]))
+        else:
+            p = ks_problem(n=n, seed=seed * 100003 + i, dtype=dtype)
+            out.append(dict(scheme=1, n=n, nsteps=int(steps), dx=p["dx"], dt=p["dt"], param=p["nu"], u0=p["u0"]))
+    return out

@@ -71,6 +71,25 @@ swept_profile_passes = _sig("swept_profile_passes", [_H, _P, _I64, _P, ctypes.PO
                                                      ctypes.POINTER(_I64)])
 swept_step_n_static = _sig("swept_step_n_static", [ctypes.POINTER(swept_config), _P, _I64, _P])
 swept_get_plan = _sig("swept_get_plan", [_H, ctypes.POINTER(swept_plan_info)])
+
+
+class swept_batch_problem(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int32), ("tile_w", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("nsteps", ctypes.c_int64), ("dx", ctypes.c_double), ("dt", ctypes.c_double),
+                ("param", ctypes.c_double)]
+
+
+SWEPT_BATCH_SPIN_LIMIT, SWEPT_BATCH_START_ITEM, SWEPT_BATCH_GRID = 1, 2, 3
+swept_batch_plan = _sig("swept_batch_plan", [ctypes.POINTER(swept_batch_problem), _I64, _I32, _I32,
+                                             ctypes.POINTER(_H)])
+swept_batch_sizes = _sig("swept_batch_sizes", [_H, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_SZ),
+                                               ctypes.POINTER(_I64)])
+swept_batch_bind_workspace = _sig("swept_batch_bind_workspace", [_H, _P, _SZ])
+swept_batch_set_option = _sig("swept_batch_set_option", [_H, _I32, _I64])
+swept_batch_run = _sig("swept_batch_run", [_H, _P, _P])
+swept_batch_sync_status = _sig("swept_batch_sync_status", [_H, _P])
+swept_batch_last_error = _sig("swept_batch_last_error", [_H, ctypes.c_char_p, _SZ])
+swept_batch_free = _sig("swept_batch_free", [_H], None)
 swept_sync_status = _sig("swept_sync_status", [_H, _P])
 swept_check_schedule = _sig("swept_check_schedule", [_H, _I64, ctypes.POINTER(_I64)])
 swept_last_error = _sig("swept_last_error", [_H, ctypes.c_char_p, _SZ])
@@ -284,3 +303,86 @@ def _swept_solve_fn():
 
     _FN = _Fn
     return _FN
+
+
+def _batch_error(b):
+    buf = ctypes.create_string_buffer(512)
+    swept_batch_last_error(b, buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+class Batch:
+    """A planned batch plus its workspace.
+
+    problems: sequence of dicts with keys scheme (HEAT/KS), n, nsteps, dx, dt,
+    param and optionally tile_w.  All states live in one 1-D tensor of
+    `state_values` values; problem i occupies [offsets[i], offsets[i] + n_i).
+    """
+
+    def __init__(self, problems, dtype, threads=0):
+        import torch
+
+        arr = (swept_batch_problem * len(problems))()
+        for i, q in enumerate(problems):
+            a = arr[i]
+            a.scheme, a.tile_w = int(q["scheme"]), int(q.get("tile_w", 0))
+            a.n, a.nsteps = int(q["n"]), int(q["nsteps"])
+            a.dx, a.dt, a.param = float(q["dx"]), float(q["dt"]), float(q["param"])
+        h = _H()
+        st = swept_batch_plan(arr, len(problems), int(dtype), int(threads), ctypes.byref(h))
+        if st != SWEPT_OK:
+            raise SweptError(st, "swept_batch_plan rejected the problems")
+        self.b = h.value
+        self.count = len(problems)
+        self.ns = [int(q["n"]) for q in problems]
+        self.dtype = dtype
+        self.torch_dtype = torch.float32 if dtype == F32 else torch.float64
+        offs = (_I64 * len(problems))()
+        sv, wb, items = _I64(), _SZ(), _I64()
+        self._check(swept_batch_sizes(self.b, offs, ctypes.byref(sv), ctypes.byref(wb), ctypes.byref(items)))
+        self.offsets = [int(x) for x in offs]
+        self.state_values, self.items = int(sv.value), int(items.value)
+        self.ws = torch.empty(max(int(wb.value), 256), dtype=torch.uint8, device="cuda")
+        self._check(swept_batch_bind_workspace(self.b, ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel()))
+
+    def _check(self, st):
+        if st != SWEPT_OK:
+            raise SweptError(st, _batch_error(self.b))
+
+    def pack(self, states):
+        """Host arrays (one per problem) -> device batch state tensor."""
+        import numpy as np
+        import torch
+
+        host = np.zeros(self.state_values, dtype=np.float64 if self.dtype == F64 else np.float32)
+        for o, n, x in zip(self.offsets, self.ns, states):
+            host[o:o + n] = x
+        return torch.from_numpy(host).cuda()
+
+    def unpack(self, u):
+        h = u.cpu().numpy()
+        return [h[o:o + n].copy() for o, n in zip(self.offsets, self.ns)]
+
+    def set_option(self, option, value):
+        self._check(swept_batch_set_option(self.b, int(option), int(value)))
+
+    def run(self, u, stream=None):
+        if not u.is_cuda or u.dtype != self.torch_dtype or u.numel() < self.state_values:
+            raise ValueError("batch state must be a CUDA tensor of %d values of %s" % (self.state_values,
+                                                                                      self.torch_dtype))
+        self._check(swept_batch_run(self.b, ctypes.c_void_p(u.data_ptr()), _stream_ptr(stream)))
+        return u
+
+    def sync_status(self, stream=None):
+        self._check(swept_batch_sync_status(self.b, _stream_ptr(stream)))
+
+    def close(self):
+        if self.b:
+            swept_batch_free(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -123,3 +123,48 @@ def test_schedule_large_pass_count(S):
     h = S.init(S.make_config(S.HEAT, S.F64, 64, 0.1, 1e-3, 1.0, tile_w=16))
     assert S.check_schedule(h, 8 * 1100 + 5) == 64 * (8 * 1100 + 5)
     S.swept_free(h)
+
+
+def test_batch_plan_layout_on_host(S):
+    from paper_1612_02495_gb300 import inputs
+
+    probs = inputs.batch_instances(inputs.batch_problems(count=16, seed=9, log2_hi=13, steps_lo=1, steps_hi=60))
+    arr = (S.swept_batch_problem * len(probs))()
+    for i, q in enumerate(probs):
+        a = arr[i]
+        a.scheme, a.n, a.nsteps, a.dx, a.dt, a.param = q["scheme"], q["n"], q["nsteps"], q["dx"], q["dt"], q["param"]
+    h = ctypes.c_void_p()
+    assert S.swept_batch_plan(arr, len(probs), S.F64, 0, ctypes.byref(h)) == S.SWEPT_OK
+    offs = (ctypes.c_int64 * len(probs))()
+    sv, wb, items = ctypes.c_int64(), ctypes.c_size_t(), ctypes.c_int64()
+    assert S.swept_batch_sizes(h, offs, ctypes.byref(sv), ctypes.byref(wb), ctypes.byref(items)) == S.SWEPT_OK
+    offs = list(offs)
+    # states are disjoint, ordered, 64-value aligned and cover the layout
+    for i, q in enumerate(probs):
+        assert offs[i] % 64 == 0
+        if i:
+            assert offs[i] >= offs[i - 1] + probs[i - 1]["n"]
+    assert sv.value >= offs[-1] + probs[-1]["n"]
+    # items = sum over problems of tiles x passes (default tile 512)
+    want = 0
+    for q in probs:
+        R, Sst = (1, 1) if q["scheme"] == 0 else (2, 2)
+        W = 512
+        hh = W // (2 * R)
+        n_sub = q["nsteps"] * Sst
+        npass = (n_sub // hh + 1 if n_sub // hh else 0) + (2 if n_sub % hh else 0)
+        want += (q["n"] // W) * npass
+    assert items.value == want
+    S.swept_batch_free(h)
+
+
+@pytest.mark.parametrize("bad", [dict(n=1002), dict(scheme=2), dict(nsteps=-1), dict(tile_w=24), dict(dt=0.0)])
+def test_batch_plan_rejects_invalid(S, bad):
+    q = dict(scheme=1, tile_w=0, n=2048, nsteps=10, dx=0.785, dt=0.005, param=1.0)
+    q.update(bad)
+    arr = (S.swept_batch_problem * 1)()
+    a = arr[0]
+    a.scheme, a.tile_w, a.n, a.nsteps, a.dx, a.dt, a.param = (q["scheme"], q["tile_w"], q["n"], q["nsteps"],
+                                                              q["dx"], q["dt"], q["param"])
+    h = ctypes.c_void_p()
+    assert S.swept_batch_plan(arr, 1, S.F64, 0, ctypes.byref(h)) == S.SWEPT_EINVAL
