@@ -166,6 +166,73 @@ def measure_adjoint(S, inputs, torch, stream, k, barrier):
             "ckpt_bytes": nb, "steps_per_pass": seg}
 
 
+def _event_time(torch, stream, fn):
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    fn()
+    b.record(stream)
+    return a, b
+
+
+def measure_fp32(S, inputs, autotune, torch, stream, barrier, ws):
+    """The same KS workload (N=2^20, 50,000 steps) in FP32: swept vs classic."""
+    p = inputs.ks_problem(n=N, dtype=np.float32)
+    t = autotune.tune_single(S.KS, S.F32, N)
+    sol = S.Solver(S.KS, S.F32, N, p["dx"], p["dt"], p["nu"], tile_w=t["tile_w"], threads=t["threads"])
+    u0 = torch.from_numpy(p["u0"]).cuda()
+    u = u0.clone()
+    res = {}
+    for name, fn in (("swept", sol.step), ("classic", sol.classic)):
+        fn(u, NSTEPS)
+        barrier()
+        ms = []
+        for _ in range(2):
+            u.copy_(u0)
+            ev = _event_time(torch, stream, lambda: fn(u, NSTEPS))
+            barrier()
+            ms.append(ev[0].elapsed_time(ev[1]))
+        res[name] = min(ms)
+    sol.sync_status()
+    sol.close()
+    return {"workload": "KS N=2^20 FP32, 50,000 steps", "tile_w": t["tile_w"], "threads": t["threads"],
+            "swept_ms": res["swept"], "classic_ms": res["classic"],
+            "swept_value": ws * N * NSTEPS / (res["swept"] * 1e-3),
+            "classic_value": ws * N * NSTEPS / (res["classic"] * 1e-3),
+            "speedup_vs_classic": res["classic"] / res["swept"]}
+
+
+def measure_batch(S, inputs, autotune, torch, stream, barrier, ws, with_f64):
+    """Batched workload: 4096 heat/KS problems, N = 2^U(10,18) rounded to 1024,
+    1,000-20,000 steps, one persistent launch per run; FP32 (and FP64 on request)."""
+    spec = inputs.batch_problems()
+    work = int((spec["n"] * spec["steps"]).sum())
+    out = {"workload": "4096 problems, N=2^U(10,18) (multiples of 1024), heat/KS 50/50, steps U{1000..20000}",
+           "cell_updates": work}
+    for dt, code, name, runs in ((np.float32, S.F32, "f32", 2), (np.float64, S.F64, "f64", 1)):
+        if code == S.F64 and not with_f64:
+            continue
+        probs = inputs.batch_instances(spec, dtype=dt)
+        plan = autotune.tune_batch(probs, code)
+        b = S.Batch(autotune.apply_batch_plan(probs, plan), code, threads=plan["threads"])
+        u0 = b.pack([q["u0"] for q in probs])
+        u = u0.clone()
+        b.run(u)
+        barrier()
+        ms = []
+        for _ in range(runs):
+            u.copy_(u0)
+            ev = _event_time(torch, stream, lambda: b.run(u))
+            barrier()
+            ms.append(ev[0].elapsed_time(ev[1]))
+        b.sync_status()
+        out[name] = {"ms": min(ms), "value": ws * work / (min(ms) * 1e-3), "unit": UNIT, "tile_w": plan["tile_w"],
+                     "threads": plan["threads"], "items": b.items}
+        b.close()
+        del u, u0
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
@@ -205,6 +272,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-classic", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-f64", action="store_true", help="also time the FP64 batch (about 50 s)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -224,8 +294,11 @@ def main():
     from paper_1612_02495_gb300 import inputs
     from paper_1612_02495_gb300 import swept as S
 
+    from paper_1612_02495_gb300 import autotune
+
     p = inputs.ks_problem(n=N, seed=1 + rank)
-    sol = S.Solver(S.KS, S.F64, N, p["dx"], p["dt"], p["nu"])
+    tuned = autotune.tune_single(S.KS, S.F64, N)
+    sol = S.Solver(S.KS, S.F64, N, p["dx"], p["dt"], p["nu"], tile_w=tuned["tile_w"], threads=tuned["threads"])
     plan = sol.plan
     stream = torch.cuda.current_stream()
     u0 = torch.from_numpy(p["u0"]).cuda()
@@ -308,6 +381,12 @@ def main():
     adjoint = None
     if not args.no_adjoint:
         adjoint = measure_adjoint(S, inputs, torch, stream, max(2, args.steps), barrier)
+    fp32 = None
+    if not args.no_fp32:
+        fp32 = measure_fp32(S, inputs, autotune, torch, stream, barrier, ws)
+    batched = None
+    if not args.no_batch:
+        batched = measure_batch(S, inputs, autotune, torch, stream, barrier, ws, args.batch_f64)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -321,6 +400,11 @@ def main():
            "roofline": roofline, "clocks": clk}
     if adjoint:
         out["adjoint"] = adjoint
+    if fp32:
+        out["fp32"] = fp32
+    if batched:
+        out["batched"] = batched
+    out["config"]["autotuned"] = {"tile_w": tuned["tile_w"], "threads": tuned["threads"]}
     if ms_classic:
         out["classic"] = {"value": ws * N * NSTEPS / (ms_classic * 1e-3), "ms_per_step": ms_classic}
         out["speedup_vs_classic"] = ms_classic / ms

@@ -1,0 +1,177 @@
+"""Autotuner for the swept plans: tile width W (which fixes the sub-timesteps
+per pass, h = W / 2r) and threads per block.
+
+The paper runs every power-of-two block size from 32 to 1024 and keeps the
+best per problem size (Section "Results").  This tuner does the same on the
+GPU at hand, by timing short probes of the real kernels with CUDA events,
+and caches the winners in a JSON file keyed by device, scheme, dtype and size.
+
+  tune_single(scheme, dtype, n, ...)  -> {"tile_w", "threads", "ms"} for swept_step_n
+  tune_batch(problems, dtype, ...)    -> {"tile_w", "threads", "ms"} for one batch plan
+
+Both only launch the library's kernels through the C ABI.
+"""
+import json
+import os
+
+import numpy as np
+
+from . import inputs
+from . import swept as S
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_1612_02495_gb300", "tune.json")
+THREADS = (32, 64, 128, 256)
+
+
+def _radius(scheme):
+    return 1 if scheme == S.HEAT else 2
+
+
+def tile_candidates(scheme, n, max_w=1024, min_w=None):
+    """Legal tile widths: multiples of 4r that divide n with at least 2 tiles
+    (powers of two, or n's other divisors when n is not a power of two);
+    widths below min_w (default: 32, or 64 from 2^16 points on) are skipped."""
+    q = 4 * _radius(scheme)
+    if min_w is None:
+        min_w = 64 if n >= (1 << 16) else 32
+    out = [w for w in range(q, max_w + 1, q) if n % w == 0 and n // w >= 2 and w >= min(min_w, n // 2)]
+    pw = [w for w in out if w & (w - 1) == 0]
+    return pw if pw else out
+
+
+def _device_key():
+    import torch
+
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return "%s/%d" % (p.name, p.multi_processor_count)
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _store(path, table):
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(table, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+
+
+def _problem(scheme, dtype, n):
+    npd = np.float64 if dtype == S.F64 else np.float32
+    if scheme == S.KS:
+        p = inputs.ks_problem(n=n, dtype=npd)
+        return p["u0"], (p["dx"], p["dt"], p["nu"]), S.BC_PERIODIC
+    if scheme == S.HEAT:
+        p = inputs.heat_problem(n=n, dtype=npd)
+        return p["u0"], (p["dx"], p["dt"], p["alpha"]), S.BC_PERIODIC
+    p = inputs.euler_problem(n=n, dtype=npd)
+    return p["U0"], (p["dx"], p["dt"], p["gamma"]), S.BC_REFLECTIVE
+
+
+def _time(fn, reps):
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b)
+        best = t if best is None else min(best, t)
+    return best
+
+
+def tune_single(scheme, dtype, n, probe_steps=None, cache=DEFAULT_CACHE, refresh=False, reps=2, threads=THREADS):
+    """Best (tile_w, threads) for swept_step_n on an n-point problem."""
+    import torch
+
+    table = _load(cache) if cache else {}
+    key = "single/%s/%d/%d/%d" % (_device_key(), scheme, dtype, n)
+    if not refresh and key in table:
+        return table[key]
+    u0, args, bc = _problem(scheme, dtype, n)
+    h_steps = max(tile_candidates(scheme, n)) // (2 * _radius(scheme))
+    steps = probe_steps or max(64, 4 * h_steps)
+    best = None
+    d0 = torch.from_numpy(np.ascontiguousarray(u0)).cuda()
+    for W in tile_candidates(scheme, n):
+        for t in threads:
+            if t > max(32, 2 * W):
+                continue
+            sol = S.Solver(scheme, dtype, n, *args, bc=bc, tile_w=W, threads=t)
+            u = d0.clone()
+            ms = _time(lambda: sol.step(u, steps), reps)
+            sol.close()
+            if best is None or ms < best["ms"]:
+                best = {"tile_w": W, "threads": t, "ms": ms, "probe_steps": steps}
+    if cache:
+        table = _load(cache)
+        table[key] = best
+        _store(cache, table)
+    return best
+
+
+def tune_batch(problems, dtype, tiles=(128, 256, 512), threads=(64, 128, 256), probe_fraction=0.05,
+               cache=DEFAULT_CACHE, refresh=False, reps=1):
+    """Best (tile_w, threads) for a batch: every candidate is timed on the whole
+    batch with each problem's step count scaled by probe_fraction (at least one
+    pass).  Candidates a problem cannot use (W not dividing n) fall back to the
+    library's default for that problem."""
+    import torch
+
+    sig = (len(problems), int(sum(q["n"] for q in problems)), int(sum(q["nsteps"] for q in problems)))
+    table = _load(cache) if cache else {}
+    key = "batch/%s/%d/%d/%d/%d" % ((_device_key(), dtype) + sig)
+    if not refresh and key in table:
+        return table[key]
+    probe = []
+    for q in problems:
+        r = dict(q)
+        r["nsteps"] = max(1, int(q["nsteps"] * probe_fraction))
+        probe.append(r)
+    best = None
+    for W in tiles:
+        for t in threads:
+            trial = []
+            for q in probe:
+                r = dict(q)
+                r["tile_w"] = W if (q["n"] % W == 0 and q["n"] // W >= 2) else 0
+                trial.append(r)
+            b = S.Batch(trial, dtype, threads=t)
+            u0 = b.pack([q["u0"] for q in problems])
+            u = u0.clone()
+            ms = _time(lambda: (u.copy_(u0), b.run(u)), reps)
+            b.close()
+            del u, u0
+            torch.cuda.empty_cache()
+            if best is None or ms < best["ms"]:
+                best = {"tile_w": W, "threads": t, "ms": ms, "probe_fraction": probe_fraction}
+    if cache:
+        table = _load(cache)
+        table[key] = best
+        _store(cache, table)
+    return best
+
+
+def apply_batch_plan(problems, plan):
+    """Problems with the tuned tile width set where it divides n (else library default)."""
+    out = []
+    for q in problems:
+        r = dict(q)
+        W = plan["tile_w"]
+        r["tile_w"] = W if (q["n"] % W == 0 and q["n"] // W >= 2) else 0
+        out.append(r)
+    return out

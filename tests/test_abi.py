@@ -168,3 +168,15 @@ def test_batch_plan_rejects_invalid(S, bad):
                                                               q["dx"], q["dt"], q["param"])
     h = ctypes.c_void_p()
     assert S.swept_batch_plan(arr, 1, S.F64, 0, ctypes.byref(h)) == S.SWEPT_EINVAL
+
+
+def test_autotune_tile_candidates(S):
+    from paper_1612_02495_gb300 import autotune
+
+    c = autotune.tile_candidates(S.KS, 1 << 20)
+    assert c == [64, 128, 256, 512, 1024]
+    assert autotune.tile_candidates(S.HEAT, 1024) == [32, 64, 128, 256, 512]
+    assert autotune.tile_candidates(S.KS, 64) == [32]
+    # a non-power-of-two size keeps its legal divisors (multiples of 4r, >= 2 tiles)
+    c = autotune.tile_candidates(S.KS, 3 * 1000)
+    assert c and all(3000 % w == 0 and w % 8 == 0 and 3000 // w >= 2 for w in c)
