@@ -39,6 +39,8 @@ FP64_INSTR_PEAK = 152 * 2 * 2.07e9
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_swept_diamond<double, KsOp> launch at
 # N = 2^20, tile 1024 (ncu, profiles/k_swept_diamond_ks_f64_n1048576.md); None once the kernel changes
 DIAMOND_TRAFFIC_BYTES = 16824832
+# same for one k_swept_persist<double, KsOp> launch (a whole solve); None until captured
+PERSIST_TRAFFIC_BYTES = None
 
 
 def peaks():
@@ -178,7 +180,8 @@ def measure_fp32(S, inputs, autotune, torch, stream, barrier, ws):
     """The same KS workload (N=2^20, 50,000 steps) in FP32: swept vs classic."""
     p = inputs.ks_problem(n=N, dtype=np.float32)
     t = autotune.tune_single(S.KS, S.F32, N)
-    sol = S.Solver(S.KS, S.F32, N, p["dx"], p["dt"], p["nu"], tile_w=t["tile_w"], threads=t["threads"])
+    sol = S.Solver(S.KS, S.F32, N, p["dx"], p["dt"], p["nu"], tile_w=t["tile_w"], threads=t["threads"],
+                   persistent=t.get("persistent", 0))
     u0 = torch.from_numpy(p["u0"]).cuda()
     u = u0.clone()
     res = {}
@@ -195,6 +198,7 @@ def measure_fp32(S, inputs, autotune, torch, stream, barrier, ws):
     sol.sync_status()
     sol.close()
     return {"workload": "KS N=2^20 FP32, 50,000 steps", "tile_w": t["tile_w"], "threads": t["threads"],
+            "persistent": t.get("persistent", 0),
             "swept_ms": res["swept"], "classic_ms": res["classic"],
             "swept_value": ws * N * NSTEPS / (res["swept"] * 1e-3),
             "classic_value": ws * N * NSTEPS / (res["classic"] * 1e-3),
@@ -298,7 +302,8 @@ def main():
 
     p = inputs.ks_problem(n=N, seed=1 + rank)
     tuned = autotune.tune_single(S.KS, S.F64, N)
-    sol = S.Solver(S.KS, S.F64, N, p["dx"], p["dt"], p["nu"], tile_w=tuned["tile_w"], threads=tuned["threads"])
+    sol = S.Solver(S.KS, S.F64, N, p["dx"], p["dt"], p["nu"], tile_w=tuned["tile_w"], threads=tuned["threads"],
+                   persistent=tuned.get("persistent", 0))
     plan = sol.plan
     stream = torch.cuda.current_stream()
     u0 = torch.from_numpy(p["u0"]).cuda()
@@ -363,20 +368,35 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e = float(t.item())
 
-    # dominant kernel: the diamond pass, timed with CUDA events on the launching stream
-    u.copy_(u0)
-    prof = sol.profile_passes(u, NSTEPS)
-    d_ms, d_n = prof["diamond"]
-    d_avg = d_ms / max(d_n, 1)
-    flops_per_diamond = FP64_FLOPS_PER_SUBSTEP * N * plan["half_cycle"]
-    achieved = flops_per_diamond / (d_avg * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": DIAMOND_TRAFFIC_BYTES,
-                "kernel": "k_swept_diamond<double, KsOp<double>>",
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured DFMA issue rate "
-                               "0.60e12/s = 1.20 TFLOP/s)",
-                "pipe_frac": (FP64_INSTR_PER_SUBSTEP * N * plan["half_cycle"] / (d_avg * 1e-3)) / FP64_INSTR_PEAK,
-                "diamond_ms_avg": d_avg, "diamond_share": d_ms / max(sum(v[0] for v in prof.values()), 1e-9)}
+    peak_src = ("derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured DFMA issue rate "
+                "0.60e12/s = 1.20 TFLOP/s)")
+    if plan.get("persistent"):
+        # dominant kernel: the persistent swept kernel, one launch per solve; its
+        # duration is the solve's event time (the launch also carries two 4-byte
+        # memsets and a one-thread status kernel)
+        units = N * 2 * NSTEPS
+        roofline = {"bound": "alu", "achieved": FP64_FLOPS_PER_SUBSTEP * units / (ms * 1e-3) / 1e12,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": PERSIST_TRAFFIC_BYTES,
+                    "kernel": "k_swept_persist<double, KsOp<double>>", "peak_source": peak_src,
+                    "pipe_frac": FP64_INSTR_PER_SUBSTEP * units / (ms * 1e-3) / FP64_INSTR_PEAK,
+                    "kernel_ms_avg": ms, "kernel_share": 1.0}
+        roofline["frac"] = roofline["achieved"] / FP64_PEAK_TFLOPS
+        launches_per_step = 2
+    else:
+        # dominant kernel: the diamond pass, timed with CUDA events on the launching stream
+        u.copy_(u0)
+        prof = sol.profile_passes(u, NSTEPS)
+        d_ms, d_n = prof["diamond"]
+        d_avg = d_ms / max(d_n, 1)
+        flops_per_diamond = FP64_FLOPS_PER_SUBSTEP * N * plan["half_cycle"]
+        achieved = flops_per_diamond / (d_avg * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": DIAMOND_TRAFFIC_BYTES,
+                    "kernel": "k_swept_diamond<double, KsOp<double>>", "peak_source": peak_src,
+                    "pipe_frac": (FP64_INSTR_PER_SUBSTEP * N * plan["half_cycle"] / (d_avg * 1e-3)) / FP64_INSTR_PEAK,
+                    "diamond_ms_avg": d_avg, "diamond_share": d_ms / max(sum(v[0] for v in prof.values()), 1e-9)}
+        if plan["tile_w"] != 1024:
+            roofline["traffic"] = None  # the ncu figure is for tile 1024
 
     adjoint = None
     if not args.no_adjoint:
@@ -404,7 +424,8 @@ def main():
         out["fp32"] = fp32
     if batched:
         out["batched"] = batched
-    out["config"]["autotuned"] = {"tile_w": tuned["tile_w"], "threads": tuned["threads"]}
+    out["config"]["autotuned"] = {"tile_w": tuned["tile_w"], "threads": tuned["threads"],
+                                  "persistent": tuned.get("persistent", 0)}
     if ms_classic:
         out["classic"] = {"value": ws * N * NSTEPS / (ms_classic * 1e-3), "ms_per_step": ms_classic}
         out["speedup_vs_classic"] = ms_classic / ms

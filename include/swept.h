@@ -76,6 +76,15 @@ typedef enum {
  *            0 = chosen by the library.  Must be a multiple of 4*r (r = 1 heat,
  *            2 KS/Euler), so that the half-cycle h = W/(2r) is even.
  *   threads  threads per block, 0 = chosen by the library (<= 1024, multiple of 32)
+ *   chunk    heat and KS: 1 = one point per thread per trip through a tier
+ *            (strided, the default); 2 = two strided points (j, j + threads)
+ *            with both windows loaded first; 3..9 (odd) = that many consecutive
+ *            points from one register window (odd so shared-memory accesses
+ *            are conflict-free)
+ *   persistent 0: one kernel launch per swept pass (graph-captured); 1: the
+ *            passes form one queue of (pass, tile) items run by a persistent
+ *            kernel whose blocks wait (bounded) only for the two tiles they read,
+ *            so no block waits for a whole pass to finish
  * Stability (Fo <= 1/2, CFL) is the caller's responsibility and is not checked.
  */
 typedef struct {
@@ -89,7 +98,9 @@ typedef struct {
   double param[4];
   int32_t tile_w;
   int32_t threads;
-  int32_t reserved[6];
+  int32_t chunk;    /* points per thread per trip: 1, 2 (strided pairs), 3, 5, 7, 9 (consecutive); 0 = 1 */
+  int32_t persistent; /* 1: swept_step_n runs all passes in one persistent kernel */
+  int32_t reserved[4];
 } swept_config;
 
 /* Plan chosen by swept_init (read-only report). */
@@ -103,6 +114,8 @@ typedef struct {
   int64_t tiles;           /* n / W */
   int64_t smem_bytes;      /* dynamic shared memory per block of the swept kernels */
   int64_t workspace_bytes; /* same as swept_workspace_size() */
+  int32_t chunk;           /* points per thread per tier */
+  int32_t persistent;      /* 1: persistent kernel */
 } swept_plan_info;
 
 typedef struct swept_handle swept_handle;

@@ -94,12 +94,14 @@ def _time(fn, reps):
     return best
 
 
-def tune_single(scheme, dtype, n, probe_steps=None, cache=DEFAULT_CACHE, refresh=False, reps=2, threads=THREADS):
-    """Best (tile_w, threads) for swept_step_n on an n-point problem."""
+def tune_single(scheme, dtype, n, probe_steps=None, cache=DEFAULT_CACHE, refresh=False, reps=2, threads=THREADS,
+                modes=(0, 1)):
+    """Best (tile_w, threads, persistent) for swept_step_n on an n-point problem
+    (persistent = 0: one launch per pass; 1: one persistent kernel)."""
     import torch
 
     table = _load(cache) if cache else {}
-    key = "single/%s/%d/%d/%d" % (_device_key(), scheme, dtype, n)
+    key = "single2/%s/%d/%d/%d" % (_device_key(), scheme, dtype, n)
     if not refresh and key in table:
         return table[key]
     u0, args, bc = _problem(scheme, dtype, n)
@@ -111,12 +113,13 @@ def tune_single(scheme, dtype, n, probe_steps=None, cache=DEFAULT_CACHE, refresh
         for t in threads:
             if t > max(32, 2 * W):
                 continue
-            sol = S.Solver(scheme, dtype, n, *args, bc=bc, tile_w=W, threads=t)
-            u = d0.clone()
-            ms = _time(lambda: sol.step(u, steps), reps)
-            sol.close()
-            if best is None or ms < best["ms"]:
-                best = {"tile_w": W, "threads": t, "ms": ms, "probe_steps": steps}
+            for mode in modes:
+                sol = S.Solver(scheme, dtype, n, *args, bc=bc, tile_w=W, threads=t, persistent=mode)
+                u = d0.clone()
+                ms = _time(lambda: sol.step(u, steps), reps)
+                sol.close()
+                if best is None or ms < best["ms"]:
+                    best = {"tile_w": W, "threads": t, "persistent": mode, "ms": ms, "probe_steps": steps}
     if cache:
         table = _load(cache)
         table[key] = best

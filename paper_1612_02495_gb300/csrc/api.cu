@@ -360,6 +360,14 @@ swept_status swept_init(const swept_config* cfg, swept_handle** out) {
   g.nt = cfg->n / W;
   g.E = 2 * g.h * g.C * 2 * R;
   g.bc = cfg->bc;
+  // one point per thread per tier unless asked: on GB300 the register-window
+  // mapping measured slower at every size (the tiers are latency-bound, and
+  // spreading a tier over more warps beats fewer shared-memory reads)
+  g.chunk = cfg->chunk > 0 ? cfg->chunk : 1;
+  if (g.chunk != 1 && g.chunk != 2 && g.chunk != 3 && g.chunk != 5 && g.chunk != 7 && g.chunk != 9) {
+    delete h;
+    return SWEPT_EINVAL;
+  }
   int th = cfg->threads > 0 ? cfg->threads : (W >= 256 ? 256 : ((W + 31) / 32) * 32);
   if (th < 32 || th > 1024 || th % 32 != 0) {
     delete h;
@@ -378,7 +386,13 @@ swept_status swept_init(const swept_config* cfg, swept_handle** out) {
   h->off_e1 = ebytes;
   h->off_tmp = 2 * ebytes;
   h->off_status = h->off_tmp + align_up((size_t)g.N * g.C * vb);
-  h->ws_bytes = h->off_status + kAlign;
+  h->off_persist = h->off_status + kAlign;
+  h->ws_bytes = h->off_persist + align_up((size_t)g.nt * sizeof(int)) + kAlign;
+  if (cfg->persistent != 0 && cfg->persistent != 1) {
+    delete h;
+    return SWEPT_EINVAL;
+  }
+  h->persistent = cfg->persistent == 1;
   (void)e;
   *out = h;
   return SWEPT_OK;
@@ -409,6 +423,33 @@ swept_status swept_step_n(swept_handle* h, void* u_dev, int64_t nsteps, void* st
   if (st != SWEPT_OK || nsteps == 0) return st;
   const cudaStream_t s = (cudaStream_t)stream;
   const int64_t n_sub = nsteps * h->g.S;
+  if (h->persistent) {
+    if (!h->persist_blocks) {
+      const int per_sm = h->impl->persist_blocks_per_sm(h->threads, h->smem);
+      if (per_sm < 1) return fail(h, SWEPT_EINVAL, "persistent kernel does not fit on an SM");
+      h->persist_blocks = per_sm * h->sm_count;
+    }
+    const Geom& g = h->g;
+    const int64_t q = n_sub / g.h, rem = n_sub % g.h;
+    const int64_t items = ((q > 0 ? q + 1 : 0) + (rem > 0 ? 2 : 0)) * g.nt;
+    const int blocks = (int)std::min<int64_t>(items, h->persist_blocks);
+    char* pc = h->ws + h->off_persist;
+    int* done = (int*)pc;
+    char* ctl = pc + align_up((size_t)g.nt * sizeof(int));
+    return run_graph(h, key_of("swept_persist", u_dev, nsteps), s, [&](cudaStream_t cs) {
+      cudaError_t e = cudaMemsetAsync(pc, 0xFF, (size_t)g.nt * sizeof(int), cs);
+      if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, 16, cs);
+      if (e == cudaSuccess)
+        e = h->impl->persist(g, h->k, u_dev, h->ws + h->off_e0, h->ws + h->off_e1, n_sub, done,
+                             (unsigned long long*)ctl, (int*)(ctl + 8), 1u << 24, blocks, h->threads, h->smem, cs);
+      // a wait that ran out is latched into the handle's status word
+      if (e == cudaSuccess) {
+        swept::k_latch_error<<<1, 1, 0, cs>>>((const int*)(ctl + 8), (int*)(h->ws + h->off_status));
+        e = cudaGetLastError();
+      }
+      return e;
+    });
+  }
   const int64_t L = swept_launch_count(h->g, n_sub);
   const int64_t kChunk = 512;  // diamond passes per cached body graph
   if (L <= 2 * kChunk + 4) {
@@ -594,6 +635,8 @@ swept_status swept_get_plan(const swept_handle* h, swept_plan_info* out) {
   out->tiles = h->g.nt;
   out->smem_bytes = (int64_t)h->smem;
   out->workspace_bytes = (int64_t)h->ws_bytes;
+  out->chunk = h->g.chunk;
+  out->persistent = h->persistent ? 1 : 0;
   return SWEPT_OK;
 }
 

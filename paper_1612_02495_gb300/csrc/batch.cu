@@ -120,6 +120,7 @@ __device__ __forceinline__ Geom geom_of(const BatchProb& p) {
   g.M = p.W + 2 * p.R;
   g.E = 2 * p.h * 2 * p.R;
   g.bc = 0;
+  g.chunk = 1;
   return g;
 }
 

@@ -27,6 +27,12 @@ struct SchemeImpl {
   // one classic sub-timestep (stage 0 or 1) from `in` into `out`
   cudaError_t (*classic)(const Geom& g, const void* k, int stage, const void* in, void* out, cudaStream_t s);
   cudaError_t (*copy)(int64_t n, const void* src, void* dst, cudaStream_t s);
+  // persistent single-problem kernel over n_sub sub-timesteps (grid = blocks)
+  cudaError_t (*persist)(const Geom& g, const void* k, void* u, void* e0, void* e1, int64_t n_sub, int* done,
+                         unsigned long long* queue, int* error, uint32_t spin_limit, int blocks, int threads,
+                         size_t smem, cudaStream_t s);
+  // co-resident blocks per SM of the persistent kernel
+  int (*persist_blocks_per_sm)(int threads, size_t smem);
   // forward passes that also record every tier into a tape (adjoint support;
   // nullptr for schemes without an adjoint)
   cudaError_t (*up_tape)(const Geom& g, const void* k, const void* u_in, void* u_out, void* e_out, int hh,

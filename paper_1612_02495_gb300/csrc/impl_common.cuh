@@ -45,6 +45,28 @@ struct Launch {
     k_copy<T><<<1024, 256, 0, s>>>(n, (const T*)src, (T*)dst);
     return cudaGetLastError();
   }
+  static cudaError_t persist(const Geom& g, const void* k, void* u, void* e0, void* e1, int64_t n_sub, int* done,
+                             unsigned long long* queue, int* error, uint32_t spin_limit, int blocks, int threads,
+                             size_t smem, cudaStream_t s) {
+    if (smem > 48 * 1024) {
+      cudaError_t e =
+          cudaFuncSetAttribute(k_swept_persist<T, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    PersistCtl c{done, queue, error, spin_limit};
+    k_swept_persist<T, Op><<<blocks, threads, smem, s>>>(g, kc(k), (T*)u, (T*)e0, (T*)e1, n_sub, c);
+    return cudaGetLastError();
+  }
+  static int persist_blocks_per_sm(int threads, size_t smem) {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_swept_persist<T, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+      return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_swept_persist<T, Op>, threads, smem) != cudaSuccess)
+      return 0;
+    return n;
+  }
   static Tape<T> mk_tape(void* tape, int64_t tier0, int64_t ntiers, int64_t base) {
     Tape<T> t;
     t.p = (T*)tape;

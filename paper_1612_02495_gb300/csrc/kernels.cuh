@@ -48,6 +48,83 @@ __device__ __forceinline__ void scalar_level(T* sm, int M, int out_row, int lo, 
   }
 }
 
+// Same tier with each thread advancing `P` consecutive points from a register
+// window of P + 2R values: shared-memory reads per point drop from 2R + 1 to
+// (P + 2R) / P, and P odd keeps the stride-P accesses free of bank conflicts.
+// Inputs past hi + R - 1 (the last one an output in [lo, hi) needs) are
+// clamped, not read; the outputs they would feed are discarded.
+template <typename T, class Op, int STAGE, int P>
+__device__ __forceinline__ void chunked_level(T* sm, int M, int out_row, int lo, int hi, const typename Op::K& k) {
+  constexpr int R = Op::R;
+  const T* in = sm + (out_row ^ 1) * M;
+  T* out = sm + out_row * M;
+  const int lim = hi + R - 1;
+  const int nch = (hi - lo + P - 1) / P;
+  for (int c = (int)threadIdx.x; c < nch; c += (int)blockDim.x) {
+    const int j0 = lo + c * P;
+    // all loads first, then all P updates in registers, then all stores, so the
+    // stores to the output row cannot order the next point's loads behind them
+    T win[P + 2 * R];
+    T p2[P];
+    T res[P];
+#pragma unroll
+    for (int q = 0; q < P + 2 * R; ++q) win[q] = in[min(j0 - R + q, lim)];
+#pragma unroll
+    for (int q = 0; q < P; ++q) p2[q] = STAGE == 1 ? out[min(j0 + q, hi - 1)] : T(0);
+#pragma unroll
+    for (int q = 0; q < P; ++q) res[q] = Op::template point<STAGE>(&win[q], p2[q], k);
+#pragma unroll
+    for (int q = 0; q < P; ++q)
+      if (j0 + q < hi) out[j0 + q] = res[q];
+  }
+}
+
+// Strided mapping with two points per thread per trip (j and j + blockDim.x):
+// both windows are loaded before either result is stored, so each thread has
+// two independent update chains in flight.
+template <typename T, class Op, int STAGE>
+__device__ __forceinline__ void strided2_level(T* sm, int M, int out_row, int lo, int hi, const typename Op::K& k) {
+  constexpr int R = Op::R;
+  const T* in = sm + (out_row ^ 1) * M;
+  T* out = sm + out_row * M;
+  const int T2 = 2 * (int)blockDim.x;
+  const int lim = hi + R - 1;
+  for (int j = lo + (int)threadIdx.x; j < hi; j += T2) {
+    const int j2 = j + (int)blockDim.x;
+    T va[2 * R + 1], vb[2 * R + 1];
+#pragma unroll
+    for (int d = 0; d <= 2 * R; ++d) {
+      va[d] = in[j + d - R];
+      vb[d] = in[min(j2 + d - R, lim)];
+    }
+    const T pa = STAGE == 1 ? out[j] : T(0);
+    const T pb = STAGE == 1 ? out[min(j2, hi - 1)] : T(0);
+    const T ra = Op::template point<STAGE>(va, pa, k);
+    const T rb = Op::template point<STAGE>(vb, pb, k);
+    out[j] = ra;
+    if (j2 < hi) out[j2] = rb;
+  }
+}
+
+template <typename T, class Op, int STAGE>
+__device__ __forceinline__ void scalar_level_any(T* sm, int M, int out_row, int lo, int hi, int wall, int chunk,
+                                                 const typename Op::K& k) {
+  if (wall != NO_WALL || chunk <= 1) {
+    scalar_level<T, Op, STAGE>(sm, M, out_row, lo, hi, wall, k);
+    return;
+  }
+  if (chunk == 2) {
+    strided2_level<T, Op, STAGE>(sm, M, out_row, lo, hi, k);
+    return;
+  }
+  switch (chunk) {
+    case 3: chunked_level<T, Op, STAGE, 3>(sm, M, out_row, lo, hi, k); break;
+    case 5: chunked_level<T, Op, STAGE, 5>(sm, M, out_row, lo, hi, k); break;
+    case 7: chunked_level<T, Op, STAGE, 7>(sm, M, out_row, lo, hi, k); break;
+    default: chunked_level<T, Op, STAGE, 9>(sm, M, out_row, lo, hi, k); break;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // one tier of Euler: primitives on [lo-2, hi+2), face fluxes on faces
 // [lo, hi] (face f between cells f-1 and f), then the cell update on [lo, hi).
@@ -126,17 +203,17 @@ __device__ __forceinline__ void euler_level(T* sm, int M, int out_row, int lo, i
 template <typename T, class Op>
 struct LevelImpl {
   __device__ __forceinline__ static void run(T* sm, int M, int stage, int out_row, int lo, int hi, int wall,
-                                             const typename Op::K& k) {
+                                             int chunk, const typename Op::K& k) {
     if (stage == 0)
-      scalar_level<T, Op, 0>(sm, M, out_row, lo, hi, wall, k);
+      scalar_level_any<T, Op, 0>(sm, M, out_row, lo, hi, wall, chunk, k);
     else
-      scalar_level<T, Op, 1>(sm, M, out_row, lo, hi, wall, k);
+      scalar_level_any<T, Op, 1>(sm, M, out_row, lo, hi, wall, chunk, k);
   }
 };
 template <typename T>
 struct LevelImpl<T, EulerOp<T>> {
   __device__ __forceinline__ static void run(T* sm, int M, int stage, int out_row, int lo, int hi, int wall,
-                                             const typename EulerOp<T>::K& k) {
+                                             int /*chunk*/, const typename EulerOp<T>::K& k) {
     if (stage == 0)
       euler_level<T, 0>(sm, M, out_row, lo, hi, wall, k);
     else
@@ -185,7 +262,7 @@ struct DevCtx {
   __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) { row(r, c)[j] = e_in[e]; }
   __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) { e_out[e] = row(r, c)[j]; }
   __device__ __forceinline__ void level(int s, int base, int lo, int hi, int64_t origin, int wall) {
-    LevelImpl<T, Op>::run(sm, g.M, stage_of(g, s), s & 1, lo, hi, wall, k);
+    LevelImpl<T, Op>::run(sm, g.M, stage_of(g, s), s & 1, lo, hi, wall, g.chunk, k);
     if (TAPE) {
       // each thread stores the values it computed itself, so no barrier is needed first
       const int64_t slot = tape.base + base + s - tape.tier0;
@@ -199,6 +276,124 @@ struct DevCtx {
     __syncthreads();
   }
 };
+
+// ---------------------------------------------------------------------------
+// persistent single-problem swept kernel: the launch sequence of
+// for_each_launch as one queue of (pass k, tile b) items, item = k * nt + b,
+// claimed in order by a grid no larger than the co-resident blocks.  Before a
+// pass-k item a block waits (bounded) until the tiles it reads have finished
+// pass k-1 (the zig-zag dependencies; they also cover reuse of the ping-pong
+// edge buffers), runs the pass phases, and publishes done[b] = k.  Global
+// reads go through L2 (ld.global.cg): other SMs write these buffers while the
+// block runs.
+// ---------------------------------------------------------------------------
+struct PersistCtl {
+  int* done;                  // nt tile counters, -1 before pass 0
+  unsigned long long* queue;  // next item
+  int* error;                 // SWEPT_ETIMEOUT (4) once a wait ran out
+  uint32_t spin_limit;
+};
+
+template <typename T, class Op>
+struct PDevCtx {
+  T* sm;
+  Geom g;
+  typename Op::K k;
+  T* u;
+  const T* e_in;
+  T* e_out;
+
+  template <class F>
+  __device__ __forceinline__ void for_range(int lo, int hi, F&& f) {
+    for (int i = lo + (int)threadIdx.x; i < hi; i += (int)blockDim.x) f(i);
+  }
+  __device__ __forceinline__ void sync() { __syncthreads(); }
+  __device__ __forceinline__ T* row(int r, int c) { return sm + (r * Op::C + c) * g.M; }
+  __device__ __forceinline__ void load_u(int r, int c, int j, int64_t x) {
+    row(r, c)[j] = __ldcg(u + c * g.N + wrap_n(x, g.N));
+  }
+  __device__ __forceinline__ void store_u(int r, int c, int j, int64_t x) { u[c * g.N + wrap_n(x, g.N)] = row(r, c)[j]; }
+  __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) { row(r, c)[j] = __ldcg(e_in + e); }
+  __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) { e_out[e] = row(r, c)[j]; }
+  __device__ __forceinline__ void level(int s, int, int lo, int hi, int64_t, int wall) {
+    LevelImpl<T, Op>::run(sm, g.M, stage_of(g, s), s & 1, lo, hi, wall, g.chunk, k);
+    __syncthreads();
+  }
+};
+
+// bounded wait for *flag >= need; gives up at the limit or once any block has
+// recorded an error
+__device__ __forceinline__ bool persist_wait(const int* flag, int need, const PersistCtl& c) {
+  for (uint32_t i = 0;; ++i) {
+    if (*(volatile const int*)flag >= need) return true;
+    if (i >= c.spin_limit || *(volatile const int*)c.error != 0) return false;
+    __nanosleep(128);
+  }
+}
+
+template <typename T, class Op>
+__global__ void __launch_bounds__(1024) k_swept_persist(Geom g, typename Op::K k, T* u, T* e0, T* e1, int64_t n_sub,
+                                                        PersistCtl ctl) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int64_t s_item;
+  __shared__ int s_ok;
+  const int q = (int)(n_sub / g.h), rem = (int)(n_sub % g.h);
+  const int main_passes = q > 0 ? q + 1 : 0;
+  const int64_t total = (int64_t)(main_passes + (rem > 0 ? 2 : 0)) * g.nt;
+  T* eb[2] = {e0, e1};
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(ctl.queue, 1ULL);
+    __syncthreads();
+    const int64_t item = s_item;
+    if (item >= total) break;
+    const int kp = (int)(item / g.nt);
+    const int64_t b = item - (int64_t)kp * g.nt;
+    if (threadIdx.x == 0) {
+      bool ok = *(volatile int*)ctl.error == 0;
+      if (ok && kp < main_passes && kp > 0) {
+        const int odd = kp & 1;
+        ok = persist_wait(ctl.done + left_tile(g, odd, b), kp - 1, ctl) &&
+             persist_wait(ctl.done + right_tile(g, odd, b), kp - 1, ctl);
+      } else if (ok && kp == main_passes && q > 0) {
+        ok = persist_wait(ctl.done + (b + g.nt - 1) % g.nt, q, ctl) && persist_wait(ctl.done + b, q, ctl) &&
+             persist_wait(ctl.done + (b + 1) % g.nt, q, ctl);
+      } else if (ok && kp == main_passes + 1) {
+        ok = persist_wait(ctl.done + b, main_passes, ctl) && persist_wait(ctl.done + (b + 1) % g.nt, main_passes, ctl);
+      }
+      if (!ok) atomicCAS(ctl.error, 0, 4);
+      s_ok = ok;
+      __threadfence();
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    PDevCtx<T, Op> cx{reinterpret_cast<T*>(smraw), g, k, u, nullptr, nullptr};
+    if (kp < main_passes) {
+      if (kp == 0) {
+        cx.e_out = eb[0];
+        run_up(cx, g, b, g.h, false);
+      } else {
+        cx.e_in = eb[(kp - 1) & 1];
+        cx.e_out = eb[kp & 1];
+        run_diamond(cx, g, b, kp & 1, kp == q ? MODE_DOWN : MODE_DIAMOND, g.h);
+      }
+    } else if (kp == main_passes) {
+      cx.e_out = eb[0];
+      run_up(cx, g, b, rem, true);
+    } else {
+      cx.e_in = eb[0];
+      cx.e_out = eb[1];
+      run_diamond(cx, g, b, 1, MODE_GAP, rem);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicExch(ctl.done + b, kp);
+  }
+}
+
+// status[0] = err[0] when err[0] is set (keeps an earlier error)
+static __global__ void k_latch_error(const int* err, int* status) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && *err != 0 && *status == 0) *status = *err;
+}
 
 template <typename T, class Op>
 __global__ void __launch_bounds__(1024) k_swept_up(Geom g, typename Op::K k, const T* u_in, T* u_out, T* e_out,

@@ -86,6 +86,7 @@ extern "C" swept_status swept_step_n_static(const swept_config* cfg, void* u_dev
   g.nt = cfg->n / W;
   g.E = 2 * g.h * g.C * 2 * R;
   g.bc = cfg->bc;
+  g.chunk = 1;
   const size_t ebytes = align_up((size_t)g.nt * g.E * im->value_bytes);
   if (2 * ebytes > kStaticScratchBytes) return SWEPT_ENOMEM_WORKSPACE;  // grid too large for the 8 MiB array
   if (nsteps == 0) return SWEPT_OK;

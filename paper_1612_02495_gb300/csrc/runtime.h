@@ -24,6 +24,9 @@ struct swept_handle {
   size_t ws_bytes = 0;   // required
   size_t ws_bound = 0;   // bound size
   size_t off_e0 = 0, off_e1 = 0, off_tmp = 0, off_status = 0;
+  size_t off_persist = 0;  // nt tile counters, then queue counter and error word
+  bool persistent = false;
+  int persist_blocks = 0;  // co-resident blocks of the persistent kernel (0 = not yet queried)
   // CUDA graphs cached by key; captured on a private stream
   cudaStream_t cap = nullptr;
   std::map<std::string, cudaGraphExec_t> graphs;

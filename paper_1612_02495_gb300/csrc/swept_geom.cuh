@@ -45,6 +45,7 @@ struct Geom {
   int M;       // W + 2R: window width
   int E;       // values per tile in an edge buffer: 2 sides * h * C * 2R
   int bc;      // 0 periodic, 1 mirror walls at -1/2 and N-1/2
+  int chunk;   // consecutive points one thread advances per tier (1 = strided mapping)
 };
 
 SW_HD int64_t floor_div(int64_t a, int64_t b) {

@@ -35,13 +35,15 @@ class swept_config(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int32), ("dtype", ctypes.c_int32), ("bc", ctypes.c_int32),
                 ("reserved0", ctypes.c_int32), ("n", ctypes.c_int64), ("dx", ctypes.c_double),
                 ("dt", ctypes.c_double), ("param", ctypes.c_double * 4), ("tile_w", ctypes.c_int32),
-                ("threads", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("threads", ctypes.c_int32), ("chunk", ctypes.c_int32), ("persistent", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class swept_plan_info(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("threads", ctypes.c_int32), ("half_cycle", ctypes.c_int32),
                 ("radius", ctypes.c_int32), ("stages", ctypes.c_int32), ("components", ctypes.c_int32),
-                ("tiles", ctypes.c_int64), ("smem_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64)]
+                ("tiles", ctypes.c_int64), ("smem_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
+                ("chunk", ctypes.c_int32), ("persistent", ctypes.c_int32)]
 
 
 _H = ctypes.c_void_p
@@ -113,12 +115,12 @@ def check(status, h=None, what=""):
         raise SweptError(status, (what + ": " if what else "") + (last_error(h) if h else ""))
 
 
-def make_config(scheme, dtype, n, dx, dt, param0, bc=BC_PERIODIC, tile_w=0, threads=0):
+def make_config(scheme, dtype, n, dx, dt, param0, bc=BC_PERIODIC, tile_w=0, threads=0, chunk=0, persistent=0):
     c = swept_config()
     c.scheme, c.dtype, c.bc, c.n = int(scheme), int(dtype), int(bc), int(n)
     c.dx, c.dt = float(dx), float(dt)
     c.param[0] = float(param0)
-    c.tile_w, c.threads = int(tile_w), int(threads)
+    c.tile_w, c.threads, c.chunk, c.persistent = int(tile_w), int(threads), int(chunk), int(persistent)
     return c
 
 
@@ -158,10 +160,10 @@ class Solver:
     float64 matching `dtype`, shape (n,) for heat/KS and (3, n) for Euler.
     """
 
-    def __init__(self, scheme, dtype, n, dx, dt, param0, bc=BC_PERIODIC, tile_w=0, threads=0):
+    def __init__(self, scheme, dtype, n, dx, dt, param0, bc=BC_PERIODIC, tile_w=0, threads=0, chunk=0, persistent=0):
         import torch
 
-        self.cfg = make_config(scheme, dtype, n, dx, dt, param0, bc, tile_w, threads)
+        self.cfg = make_config(scheme, dtype, n, dx, dt, param0, bc, tile_w, threads, chunk, persistent)
         self.h = init(self.cfg)
         self.scheme, self.dtype, self.n = scheme, dtype, n
         self.torch_dtype = torch.float32 if dtype == F32 else torch.float64

@@ -182,3 +182,111 @@ def test_ks_full_size_sampled(S):
         k = reach + 8
         assert loc[k] == fin[c], (c, loc[k], fin[c])
     sol.close()
+
+
+@pytest.mark.parametrize("chunk", [1, 3, 5, 7, 9])
+@pytest.mark.parametrize("scheme,dtype", [("ks", np.float64), ("ks", np.float32), ("heat", np.float64),
+                                          ("heat", np.float32)])
+def test_chunked_tiers_parity(S, chunk, scheme, dtype):
+    """Each thread advancing `chunk` consecutive points from a register window
+    gives the same bits as the strided mapping and the oracle (ragged tiers:
+    widths not multiples of the chunk, tile 96/192, thread counts below the
+    chunk count)."""
+    code = S.F64 if dtype == np.float64 else S.F32
+    if scheme == "ks":
+        p = inputs.ks_problem(n=192 * 8, dtype=dtype)
+        sw, cl, plan = None, None, None
+        import torch
+
+        sol = S.Solver(S.KS, code, p["u0"].size, p["dx"], p["dt"], p["nu"], tile_w=192, threads=32, chunk=chunk)
+        ref = oracle.ks(p["u0"], p["dx"], p["dt"], p["nu"], 333)
+    else:
+        p = inputs.heat_problem(n=96 * 10, dtype=dtype)
+        import torch
+
+        sol = S.Solver(S.HEAT, code, p["u0"].size, p["dx"], p["dt"], p["alpha"], tile_w=96, threads=32, chunk=chunk)
+        ref = oracle.heat(p["u0"], p["dx"], p["dt"], p["alpha"], 333)
+    assert sol.plan["chunk"] == chunk
+    u = torch.from_numpy(p["u0"]).cuda()
+    sol.step(u, 333)
+    torch.cuda.synchronize()
+    sol.sync_status()
+    assert np.array_equal(u.cpu().numpy(), ref)
+    sol.close()
+
+
+PERSIST_CASES = [
+    # scheme, dtype, n, W, threads, nsteps, bc
+    ("heat", np.float64, 1024, 64, 64, 10000, 0),
+    ("heat", np.float32, 8 * 24, 8, 32, 101, 1),
+    ("ks", np.float64, 2048, 64, 64, 1003, 0),
+    ("ks", np.float32, 3 * 128, 128, 128, 257, 0),
+    ("ks", np.float64, 1 << 16, 512, 128, 701, 0),
+    ("ks", np.float64, 2 * 32, 32, 32, 3, 0),       # remainder only
+    ("euler", np.float64, 1024, 64, 64, 300, 1),
+    ("euler", np.float64, 1024, 64, 64, 300, 0),
+    ("euler", np.float32, 3 * 32, 32, 32, 77, 1),
+]
+
+
+@pytest.mark.parametrize("scheme,dtype,n,W,threads,nsteps,bc", PERSIST_CASES)
+def test_persistent_mode_parity(S, scheme, dtype, n, W, threads, nsteps, bc):
+    """swept_step_n with the persistent kernel (one queue of pass x tile items)
+    equals the per-pass launches, classic and the oracle bit for bit."""
+    import torch
+
+    code = S.F64 if dtype == np.float64 else S.F32
+    if scheme == "heat":
+        p = inputs.heat_problem(n=n, dtype=dtype)
+        u0, args, sc = p["u0"], (p["dx"], p["dt"], p["alpha"]), S.HEAT
+        ref = oracle.heat(u0, p["dx"], p["dt"], p["alpha"], nsteps, bc=bc)
+    elif scheme == "ks":
+        p = inputs.ks_problem(n=n, dtype=dtype)
+        u0, args, sc = p["u0"], (p["dx"], p["dt"], p["nu"]), S.KS
+        ref = oracle.ks(u0, p["dx"], p["dt"], p["nu"], nsteps, threads=THREADS)
+    else:
+        pr = inputs.euler_problem(n=n, dtype=dtype)
+        u0 = pr["U0"]
+        if bc == 0:
+            x = (np.arange(n) + 0.5) / n
+            rho = 1 + 0.2 * np.sin(2 * np.pi * x)
+            uu = 0.3 + 0.1 * np.cos(2 * np.pi * x)
+            pp = 1 + 0.1 * np.sin(4 * np.pi * x)
+            u0 = np.stack([rho, rho * uu, pp / 0.4 + 0.5 * rho * uu * uu]).astype(dtype)
+        args, sc = (pr["dx"], pr["dt"], pr["gamma"]), S.EULER
+        ref = oracle.euler(u0, pr["dx"], pr["dt"], pr["gamma"], nsteps, bc=bc, threads=THREADS)
+    sol = S.Solver(sc, code, n, *args, bc=bc, tile_w=W, threads=threads, persistent=1)
+    assert sol.plan["persistent"] == 1
+    u = torch.from_numpy(np.ascontiguousarray(u0)).cuda()
+    v = u.clone()
+    sol.step(u, nsteps)
+    sol.classic(v, nsteps)
+    torch.cuda.synchronize()
+    sol.sync_status()
+    assert np.array_equal(u.cpu().numpy(), v.cpu().numpy())
+    assert np.array_equal(u.cpu().numpy(), ref)
+    # a second call continues from the state (graph replay, counters reset)
+    sol.step(u, 7)
+    sol.classic(v, 7)
+    torch.cuda.synchronize()
+    assert np.array_equal(u.cpu().numpy(), v.cpu().numpy())
+    sol.close()
+
+
+def test_persistent_full_size_ks(S):
+    """KS N=2^20 FP64, 50,000 steps in the persistent kernel equals the per-pass path."""
+    import torch
+
+    n = 1 << 20
+    p = inputs.ks_problem(n=n)
+    a = S.Solver(S.KS, S.F64, n, p["dx"], p["dt"], p["nu"], tile_w=512, threads=128, persistent=1)
+    b = S.Solver(S.KS, S.F64, n, p["dx"], p["dt"], p["nu"], tile_w=1024, threads=32)
+    u = torch.from_numpy(p["u0"]).cuda()
+    v = u.clone()
+    a.step(u, 50000)
+    b.step(v, 50000)
+    torch.cuda.synchronize()
+    a.sync_status()
+    assert np.array_equal(u.cpu().numpy(), v.cpu().numpy())
+    a.close()
+    b.close()
