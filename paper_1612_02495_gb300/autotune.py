@@ -101,7 +101,7 @@ def tune_single(scheme, dtype, n, probe_steps=None, cache=DEFAULT_CACHE, refresh
     import torch
 
     table = _load(cache) if cache else {}
-    key = "single2/%s/%d/%d/%d" % (_device_key(), scheme, dtype, n)
+    key = "single2/%s/%d/%d/%d/%s" % (_device_key(), scheme, dtype, n, probe_steps)
     if not refresh and key in table:
         return table[key]
     u0, args, bc = _problem(scheme, dtype, n)
