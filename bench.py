@@ -55,6 +55,22 @@ def peaks():
         return {}
 
 
+def max_over_ranks(value, dist, ws, device="cuda"):
+    """Largest `value` over all ranks (the whole job takes as long as its slowest rank)."""
+    if ws <= 1:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(work_per_rank, ms_max, ws):
+    """Units processed by all ranks (each rank runs its own replica) per second."""
+    return ws * work_per_rank / (ms_max * 1e-3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -338,19 +354,14 @@ def main():
         barrier()
         for a, b in evs:
             total += a.elapsed_time(b)
-        ms = total / k
-        if ws > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(total / k, dist, ws)
 
     clocks = Clocks(local)
     clocks.start()
     ms = timed(lambda x: sol.step(x, NSTEPS), args.steps, args.warmup)
     clk = clocks.stop()
     sol.sync_status()
-    value = ws * N * NSTEPS / (ms * 1e-3)
+    value = whole_job_rate(N * NSTEPS, ms, ws)
 
     ms_classic = None
     if not args.no_classic:
@@ -366,11 +377,7 @@ def main():
         t0 = time.perf_counter()
         sol.run_host(h_in, h_out, u, NSTEPS)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e = float(np.mean(e2e_ms))
-    if ws > 1:
-        t = torch.tensor([e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = float(t.item())
+    e2e = max_over_ranks(float(np.mean(e2e_ms)), dist, ws)
 
     peak_src = ("derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (measured DFMA issue rate "
                 "0.60e12/s = 1.20 TFLOP/s)")
