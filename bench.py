@@ -201,7 +201,7 @@ def measure_fp32(S, inputs, autotune, torch, stream, barrier, ws):
     p = inputs.ks_problem(n=N, dtype=np.float32)
     t = autotune.tune_single(S.KS, S.F32, N, probe_steps=8000)
     sol = S.Solver(S.KS, S.F32, N, p["dx"], p["dt"], p["nu"], tile_w=t["tile_w"], threads=t["threads"],
-                   persistent=t.get("persistent", 0))
+                   persistent=t.get("persistent", 0), cluster=t.get("cluster", 0))
     u0 = torch.from_numpy(p["u0"]).cuda()
     u = u0.clone()
     res = {}
@@ -323,7 +323,7 @@ def main():
     p = inputs.ks_problem(n=N, seed=1 + rank)
     tuned = autotune.tune_single(S.KS, S.F64, N, probe_steps=4000)
     sol = S.Solver(S.KS, S.F64, N, p["dx"], p["dt"], p["nu"], tile_w=tuned["tile_w"], threads=tuned["threads"],
-                   persistent=tuned.get("persistent", 0))
+                   persistent=tuned.get("persistent", 0), cluster=tuned.get("cluster", 0))
     plan = sol.plan
     stream = torch.cuda.current_stream()
     u0 = torch.from_numpy(p["u0"]).cuda()

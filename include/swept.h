@@ -85,6 +85,10 @@ typedef enum {
  *            passes form one queue of (pass, tile) items run by a persistent
  *            kernel whose blocks wait (bounded) only for the two tiles they read,
  *            so no block waits for a whole pass to finish
+ *   cluster  1: (n / tile_w <= 16) one launch whose blocks form a single
+ *            thread-block cluster; each block keeps its tile in shared memory
+ *            for the whole solve and reads its neighbour's edges through
+ *            distributed shared memory, with a cluster barrier between passes
  * Stability (Fo <= 1/2, CFL) is the caller's responsibility and is not checked.
  */
 typedef struct {
@@ -100,7 +104,8 @@ typedef struct {
   int32_t threads;
   int32_t chunk;    /* points per thread per trip: 1, 2 (strided pairs), 3, 5, 7, 9 (consecutive); 0 = 1 */
   int32_t persistent; /* 1: swept_step_n runs all passes in one persistent kernel */
-  int32_t reserved[4];
+  int32_t cluster;    /* 1: the whole grid (2..16 tiles) is one thread-block cluster */
+  int32_t reserved[3];
 } swept_config;
 
 /* Plan chosen by swept_init (read-only report). */
@@ -116,6 +121,8 @@ typedef struct {
   int64_t workspace_bytes; /* same as swept_workspace_size() */
   int32_t chunk;           /* points per thread per tier */
   int32_t persistent;      /* 1: persistent kernel */
+  int32_t cluster;         /* 1: single-cluster kernel */
+  int32_t reserved;
 } swept_plan_info;
 
 typedef struct swept_handle swept_handle;

@@ -21,6 +21,7 @@ from . import swept as S
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_1612_02495_gb300", "tune.json")
 THREADS = (32, 64, 128, 256)
+MAX_CLUSTER_TILES = 16  # the largest (non-portable) thread-block cluster
 
 
 def _radius(scheme):
@@ -95,13 +96,15 @@ def _time(fn, reps):
 
 
 def tune_single(scheme, dtype, n, probe_steps=None, cache=DEFAULT_CACHE, refresh=False, reps=2, threads=THREADS,
-                modes=(0, 1)):
-    """Best (tile_w, threads, persistent) for swept_step_n on an n-point problem
-    (persistent = 0: one launch per pass; 1: one persistent kernel)."""
+                modes=(0, 1, 2)):
+    """Best (tile_w, threads, persistent, cluster) for swept_step_n on an
+    n-point problem.  Modes: 0 one launch per pass; 1 one persistent kernel;
+    2 one thread-block cluster holding every tile (tried only with at most
+    MAX_CLUSTER_TILES tiles)."""
     import torch
 
     table = _load(cache) if cache else {}
-    key = "single2/%s/%d/%d/%d/%s" % (_device_key(), scheme, dtype, n, probe_steps)
+    key = "single3/%s/%d/%d/%d/%s" % (_device_key(), scheme, dtype, n, probe_steps)
     if not refresh and key in table:
         return table[key]
     u0, args, bc = _problem(scheme, dtype, n)
@@ -114,12 +117,19 @@ def tune_single(scheme, dtype, n, probe_steps=None, cache=DEFAULT_CACHE, refresh
             if t > max(32, 2 * W):
                 continue
             for mode in modes:
-                sol = S.Solver(scheme, dtype, n, *args, bc=bc, tile_w=W, threads=t, persistent=mode)
+                if mode == 2 and n // W > MAX_CLUSTER_TILES:
+                    continue
+                try:
+                    sol = S.Solver(scheme, dtype, n, *args, bc=bc, tile_w=W, threads=t, persistent=int(mode == 1),
+                                   cluster=int(mode == 2))
+                except S.SweptError:
+                    continue  # e.g. a cluster window that does not fit in shared memory
                 u = d0.clone()
                 ms = _time(lambda: sol.step(u, steps), reps)
                 sol.close()
                 if best is None or ms < best["ms"]:
-                    best = {"tile_w": W, "threads": t, "persistent": mode, "ms": ms, "probe_steps": steps}
+                    best = {"tile_w": W, "threads": t, "persistent": int(mode == 1), "cluster": int(mode == 2),
+                            "ms": ms, "probe_steps": steps}
     if cache:
         table = _load(cache)
         table[key] = best

@@ -393,6 +393,16 @@ swept_status swept_init(const swept_config* cfg, swept_handle** out) {
     return SWEPT_EINVAL;
   }
   h->persistent = cfg->persistent == 1;
+  if (cfg->cluster != 0 && cfg->cluster != 1) {
+    delete h;
+    return SWEPT_EINVAL;
+  }
+  h->cluster = cfg->cluster == 1;
+  if (h->cluster && (g.nt > 16 || h->persistent ||
+                     h->smem + 2 * (size_t)g.E * im->value_bytes > (size_t)max_smem)) {
+    delete h;
+    return SWEPT_EINVAL;
+  }
   (void)e;
   *out = h;
   return SWEPT_OK;
@@ -423,6 +433,11 @@ swept_status swept_step_n(swept_handle* h, void* u_dev, int64_t nsteps, void* st
   if (st != SWEPT_OK || nsteps == 0) return st;
   const cudaStream_t s = (cudaStream_t)stream;
   const int64_t n_sub = nsteps * h->g.S;
+  if (h->cluster) {
+    return run_graph(h, key_of("swept_cluster", u_dev, nsteps), s, [&](cudaStream_t cs) {
+      return h->impl->cluster(h->g, h->k, u_dev, n_sub, h->threads, h->smem, cs);
+    });
+  }
   if (h->persistent) {
     if (!h->persist_blocks) {
       const int per_sm = h->impl->persist_blocks_per_sm(h->threads, h->smem);
@@ -637,6 +652,8 @@ swept_status swept_get_plan(const swept_handle* h, swept_plan_info* out) {
   out->workspace_bytes = (int64_t)h->ws_bytes;
   out->chunk = h->g.chunk;
   out->persistent = h->persistent ? 1 : 0;
+  out->cluster = h->cluster ? 1 : 0;
+  out->reserved = 0;
   return SWEPT_OK;
 }
 

@@ -33,6 +33,9 @@ struct SchemeImpl {
                          size_t smem, cudaStream_t s);
   // co-resident blocks per SM of the persistent kernel
   int (*persist_blocks_per_sm)(int threads, size_t smem);
+  // whole solve in one cluster of g.nt (<= 16) blocks, edges through DSMEM
+  cudaError_t (*cluster)(const Geom& g, const void* k, void* u, int64_t n_sub, int threads, size_t smem,
+                         cudaStream_t s);
   // forward passes that also record every tier into a tape (adjoint support;
   // nullptr for schemes without an adjoint)
   cudaError_t (*up_tape)(const Geom& g, const void* k, const void* u_in, void* u_out, void* e_out, int hh,

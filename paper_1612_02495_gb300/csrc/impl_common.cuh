@@ -67,6 +67,30 @@ struct Launch {
       return 0;
     return n;
   }
+  // smem = window bytes; the two export areas (2 E values) are added here
+  static cudaError_t cluster(const Geom& g, const void* k, void* u, int64_t n_sub, int threads, size_t smem,
+                             cudaStream_t s) {
+    const int64_t win_values = (int64_t)(smem / sizeof(T));
+    const size_t bytes = smem + 2 * (size_t)g.E * sizeof(T);
+    auto fn = k_swept_cluster<T, Op>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess && bytes > 48 * 1024)
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)g.nt, 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = bytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)g.nt;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, g, kc(k), (T*)u, n_sub, win_values);
+  }
   static Tape<T> mk_tape(void* tape, int64_t tier0, int64_t ntiers, int64_t base) {
     Tape<T> t;
     t.p = (T*)tape;

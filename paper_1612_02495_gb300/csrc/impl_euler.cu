@@ -32,7 +32,7 @@ template <typename T>
 SchemeImpl make_euler() {
   using L = Launch<T, EulerOp<T>>;
   SchemeImpl im{2, 2, 3, (int)sizeof(T), euler_consts<T>, L::smem_values, L::prepare, L::up, L::diamond,
-                euler_classic<T>, L::copy, L::persist, L::persist_blocks_per_sm, L::up_tape, L::diamond_tape, nullptr,
+                euler_classic<T>, L::copy, L::persist, L::persist_blocks_per_sm, L::cluster, L::up_tape, L::diamond_tape, nullptr,
                 nullptr, nullptr, nullptr};
   return im;
 }

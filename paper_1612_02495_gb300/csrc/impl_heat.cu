@@ -28,7 +28,7 @@ template <typename T>
 SchemeImpl make_heat() {
   using L = Launch<T, HeatOp<T>>;
   SchemeImpl im{1, 1, 1, (int)sizeof(T), heat_consts<T>, L::smem_values, L::prepare, L::up, L::diamond,
-                L::classic, L::copy, L::persist, L::persist_blocks_per_sm, L::up_tape, L::diamond_tape, nullptr,
+                L::classic, L::copy, L::persist, L::persist_blocks_per_sm, L::cluster, L::up_tape, L::diamond_tape, nullptr,
                 nullptr, nullptr, nullptr};
   return im;
 }

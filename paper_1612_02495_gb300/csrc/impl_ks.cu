@@ -36,7 +36,7 @@ template <typename T>
 SchemeImpl make_ks() {
   using L = Launch<T, KsOp<T>>;
   SchemeImpl im{2, 2, 1, (int)sizeof(T), ks_consts<T>, L::smem_values, L::prepare, L::up, L::diamond,
-                L::classic, L::copy, L::persist, L::persist_blocks_per_sm, L::up_tape, L::diamond_tape, nullptr,
+                L::classic, L::copy, L::persist, L::persist_blocks_per_sm, L::cluster, L::up_tape, L::diamond_tape, nullptr,
                 nullptr, nullptr, nullptr};
   return im;
 }

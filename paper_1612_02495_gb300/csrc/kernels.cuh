@@ -1,6 +1,7 @@
 // CUDA kernels: swept passes (up-triangle, diamond, down/gap) and the classic
 // one-sub-timestep kernel, templated on the value type and the scheme operator.
 #pragma once
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -387,6 +388,82 @@ __global__ void __launch_bounds__(1024) k_swept_persist(Geom g, typename Op::K k
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) atomicExch(ctl.done + b, kp);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// cluster-resident swept kernel: the whole grid (nt <= 16 tiles) is one
+// thread-block cluster, block b owning tile b for the entire solve.  Edges are
+// exported into a ping-pong area of the block's own shared memory and read by
+// the neighbour block straight from there through distributed shared memory
+// (cluster.map_shared_rank); a cluster barrier separates the passes.  No
+// global edge buffers and no per-pass launches.  The state is read at the
+// first pass and written by the down-triangle and remainder passes only.
+// ---------------------------------------------------------------------------
+template <typename T, class Op>
+struct ClusterCtx {
+  T* sm;         // the block's window rows (and Euler scratch)
+  T* ex_in;      // export area of the previous pass (read remotely)
+  T* ex_out;     // export area this pass writes (own tile's edges)
+  Geom g;
+  typename Op::K k;
+  T* u;
+  unsigned my_rank;
+
+  template <class F>
+  __device__ __forceinline__ void for_range(int lo, int hi, F&& f) {
+    for (int i = lo + (int)threadIdx.x; i < hi; i += (int)blockDim.x) f(i);
+  }
+  __device__ __forceinline__ void sync() { __syncthreads(); }
+  __device__ __forceinline__ T* row(int r, int c) { return sm + (r * Op::C + c) * g.M; }
+  __device__ __forceinline__ void load_u(int r, int c, int j, int64_t x) {
+    row(r, c)[j] = __ldcg(u + c * g.N + wrap_n(x, g.N));
+  }
+  __device__ __forceinline__ void store_u(int r, int c, int j, int64_t x) { u[c * g.N + wrap_n(x, g.N)] = row(r, c)[j]; }
+  __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) {
+    const unsigned tile = (unsigned)(e / g.E);
+    const T* src = cooperative_groups::this_cluster().map_shared_rank(ex_in + (e - (int64_t)tile * g.E), tile);
+    row(r, c)[j] = *src;
+  }
+  __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) {
+    ex_out[e - (int64_t)my_rank * g.E] = row(r, c)[j];
+  }
+  __device__ __forceinline__ void level(int s, int, int lo, int hi, int64_t, int wall) {
+    LevelImpl<T, Op>::run(sm, g.M, stage_of(g, s), s & 1, lo, hi, wall, g.chunk, k);
+    __syncthreads();
+  }
+};
+
+template <typename T, class Op>
+__global__ void __launch_bounds__(1024) k_swept_cluster(Geom g, typename Op::K k, T* u, int64_t n_sub,
+                                                        int64_t smem_values) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  T* sm = reinterpret_cast<T*>(smraw);
+  T* ex[2] = {sm + smem_values, sm + smem_values + g.E};
+  const unsigned b = cluster.block_rank();
+  ClusterCtx<T, Op> cx{sm, ex[1], ex[0], g, k, u, b};
+  const int q = (int)(n_sub / g.h), rem = (int)(n_sub % g.h);
+  if (q > 0) {
+    cx.ex_out = ex[0];
+    run_up(cx, g, (int64_t)b, g.h, false);
+    cluster.sync();
+    for (int p = 1; p <= q; ++p) {
+      cx.ex_in = ex[(p - 1) & 1];
+      cx.ex_out = ex[p & 1];
+      run_diamond(cx, g, (int64_t)b, p & 1, p == q ? MODE_DOWN : MODE_DIAMOND, g.h);
+      cluster.sync();  // edges of pass p complete (and, after the down pass, the state)
+    }
+  }
+  if (rem > 0) {
+    cx.ex_out = ex[0];
+    run_up(cx, g, (int64_t)b, rem, true);
+    cluster.sync();
+    cx.ex_in = ex[0];
+    cx.ex_out = ex[1];
+    run_diamond(cx, g, (int64_t)b, 1, MODE_GAP, rem);
+    cluster.sync();  // keep every block's shared memory alive until its edges were read
   }
 }
 

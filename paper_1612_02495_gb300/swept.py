@@ -36,14 +36,15 @@ class swept_config(ctypes.Structure):
                 ("reserved0", ctypes.c_int32), ("n", ctypes.c_int64), ("dx", ctypes.c_double),
                 ("dt", ctypes.c_double), ("param", ctypes.c_double * 4), ("tile_w", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("chunk", ctypes.c_int32), ("persistent", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("cluster", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class swept_plan_info(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("threads", ctypes.c_int32), ("half_cycle", ctypes.c_int32),
                 ("radius", ctypes.c_int32), ("stages", ctypes.c_int32), ("components", ctypes.c_int32),
                 ("tiles", ctypes.c_int64), ("smem_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
-                ("chunk", ctypes.c_int32), ("persistent", ctypes.c_int32)]
+                ("chunk", ctypes.c_int32), ("persistent", ctypes.c_int32), ("cluster", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _H = ctypes.c_void_p
@@ -115,12 +116,14 @@ def check(status, h=None, what=""):
         raise SweptError(status, (what + ": " if what else "") + (last_error(h) if h else ""))
 
 
-def make_config(scheme, dtype, n, dx, dt, param0, bc=BC_PERIODIC, tile_w=0, threads=0, chunk=0, persistent=0):
+def make_config(scheme, dtype, n, dx, dt, param0, bc=BC_PERIODIC, tile_w=0, threads=0, chunk=0, persistent=0,
+                cluster=0):
     c = swept_config()
     c.scheme, c.dtype, c.bc, c.n = int(scheme), int(dtype), int(bc), int(n)
     c.dx, c.dt = float(dx), float(dt)
     c.param[0] = float(param0)
     c.tile_w, c.threads, c.chunk, c.persistent = int(tile_w), int(threads), int(chunk), int(persistent)
+    c.cluster = int(cluster)
     return c
 
 
@@ -160,10 +163,11 @@ class Solver:
     float64 matching `dtype`, shape (n,) for heat/KS and (3, n) for Euler.
     """
 
-    def __init__(self, scheme, dtype, n, dx, dt, param0, bc=BC_PERIODIC, tile_w=0, threads=0, chunk=0, persistent=0):
+    def __init__(self, scheme, dtype, n, dx, dt, param0, bc=BC_PERIODIC, tile_w=0, threads=0, chunk=0, persistent=0,
+                 cluster=0):
         import torch
 
-        self.cfg = make_config(scheme, dtype, n, dx, dt, param0, bc, tile_w, threads, chunk, persistent)
+        self.cfg = make_config(scheme, dtype, n, dx, dt, param0, bc, tile_w, threads, chunk, persistent, cluster)
         self.h = init(self.cfg)
         self.scheme, self.dtype, self.n = scheme, dtype, n
         self.torch_dtype = torch.float32 if dtype == F32 else torch.float64

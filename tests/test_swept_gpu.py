@@ -290,3 +290,60 @@ def test_persistent_full_size_ks(S):
     assert np.array_equal(u.cpu().numpy(), v.cpu().numpy())
     a.close()
     b.close()
+
+
+CLUSTER_CASES = [
+    # scheme, dtype, n, W, threads, nsteps, bc
+    ("heat", np.float64, 1024, 64, 64, 10000, 0),    # the heat workload: 16 tiles = one 16-block cluster
+    ("heat", np.float32, 1024, 64, 64, 333, 1),      # insulated ends
+    ("heat", np.float64, 3 * 32, 32, 32, 101, 0),    # cluster of 3
+    ("ks", np.float64, 1 << 14, 1024, 256, 2001, 0),  # KS 2^14 as 16 tiles of 1024
+    ("ks", np.float32, 2 * 64, 64, 64, 77, 0),       # cluster of 2
+    ("ks", np.float64, 5 * 128, 128, 128, 3, 0),     # remainder only
+    ("euler", np.float64, 4 * 64, 64, 64, 300, 1),   # reflective walls at the split block
+    ("euler", np.float32, 8 * 32, 32, 32, 41, 0),
+]
+
+
+@pytest.mark.parametrize("scheme,dtype,n,W,threads,nsteps,bc", CLUSTER_CASES)
+def test_cluster_mode_parity(S, scheme, dtype, n, W, threads, nsteps, bc):
+    """All tiles in one thread-block cluster, edges through distributed shared
+    memory: equal to classic and the oracle bit for bit."""
+    import torch
+
+    code = S.F64 if dtype == np.float64 else S.F32
+    if scheme == "heat":
+        p = inputs.heat_problem(n=n, dtype=dtype)
+        u0, args, sc = p["u0"], (p["dx"], p["dt"], p["alpha"]), S.HEAT
+        ref = oracle.heat(u0, p["dx"], p["dt"], p["alpha"], nsteps, bc=bc)
+    elif scheme == "ks":
+        p = inputs.ks_problem(n=n, dtype=dtype)
+        u0, args, sc = p["u0"], (p["dx"], p["dt"], p["nu"]), S.KS
+        ref = oracle.ks(u0, p["dx"], p["dt"], p["nu"], nsteps, threads=THREADS)
+    else:
+        pr = inputs.euler_problem(n=n, dtype=dtype)
+        u0 = pr["U0"]
+        if bc == 0:
+            x = (np.arange(n) + 0.5) / n
+            rho = 1 + 0.2 * np.sin(2 * np.pi * x)
+            uu = 0.3 + 0.1 * np.cos(2 * np.pi * x)
+            pp = 1 + 0.1 * np.sin(4 * np.pi * x)
+            u0 = np.stack([rho, rho * uu, pp / 0.4 + 0.5 * rho * uu * uu]).astype(dtype)
+        args, sc = (pr["dx"], pr["dt"], pr["gamma"]), S.EULER
+        ref = oracle.euler(u0, pr["dx"], pr["dt"], pr["gamma"], nsteps, bc=bc, threads=THREADS)
+    sol = S.Solver(sc, code, n, *args, bc=bc, tile_w=W, threads=threads, cluster=1)
+    assert sol.plan["cluster"] == 1
+    u = torch.from_numpy(np.ascontiguousarray(u0)).cuda()
+    v = u.clone()
+    sol.step(u, nsteps)
+    sol.classic(v, nsteps)
+    torch.cuda.synchronize()
+    sol.sync_status()
+    assert np.array_equal(u.cpu().numpy(), v.cpu().numpy())
+    assert np.array_equal(u.cpu().numpy(), ref)
+    sol.close()
+
+
+def test_cluster_mode_rejects_more_than_16_tiles(S):
+    with pytest.raises(S.SweptError):
+        S.Solver(S.KS, S.F64, 17 * 64, 0.785, 0.005, 1.0, tile_w=64, cluster=1)
