@@ -67,6 +67,7 @@ struct BatchDev {
 // this persistent block runs and L1 is not coherent.
 template <typename T, class Op>
 struct BatchCtx {
+  static constexpr int kR = Op::R, kC = Op::C;
   T* sm;
   Geom g;
   typename Op::K k;
@@ -87,7 +88,7 @@ struct BatchCtx {
   __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) { row(r, c)[j] = __ldcg(e_in + e); }
   __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) { e_out[e] = row(r, c)[j]; }
   __device__ __forceinline__ void level(int s, int, int lo, int hi, int64_t, int wall) {
-    if (stage_of(g, s) == 0)
+    if (stage_c<Op>(s) == 0)
       scalar_tier<0>(lo, hi, s & 1, wall);
     else
       scalar_tier<1>(lo, hi, s & 1, wall);

@@ -69,6 +69,7 @@ struct Sim {
 };
 
 struct HostCtx {
+  static constexpr int kR = 0, kC = 0;  // stencil constants from the geometry
   Sim& sim;
   const Geom& g;
   int64_t block;

@@ -239,6 +239,7 @@ struct Tape {
 
 template <typename T, class Op, bool TAPE = false>
 struct DevCtx {
+  static constexpr int kR = Op::R, kC = Op::C;
   T* sm;
   Geom g;
   typename Op::K k;
@@ -263,7 +264,7 @@ struct DevCtx {
   __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) { row(r, c)[j] = e_in[e]; }
   __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) { e_out[e] = row(r, c)[j]; }
   __device__ __forceinline__ void level(int s, int base, int lo, int hi, int64_t origin, int wall) {
-    LevelImpl<T, Op>::run(sm, g.M, stage_of(g, s), s & 1, lo, hi, wall, g.chunk, k);
+    LevelImpl<T, Op>::run(sm, g.M, stage_c<Op>(s), s & 1, lo, hi, wall, g.chunk, k);
     if (TAPE) {
       // each thread stores the values it computed itself, so no barrier is needed first
       const int64_t slot = tape.base + base + s - tape.tier0;
@@ -297,6 +298,7 @@ struct PersistCtl {
 
 template <typename T, class Op>
 struct PDevCtx {
+  static constexpr int kR = Op::R, kC = Op::C;
   T* sm;
   Geom g;
   typename Op::K k;
@@ -317,7 +319,7 @@ struct PDevCtx {
   __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) { row(r, c)[j] = __ldcg(e_in + e); }
   __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) { e_out[e] = row(r, c)[j]; }
   __device__ __forceinline__ void level(int s, int, int lo, int hi, int64_t, int wall) {
-    LevelImpl<T, Op>::run(sm, g.M, stage_of(g, s), s & 1, lo, hi, wall, g.chunk, k);
+    LevelImpl<T, Op>::run(sm, g.M, stage_c<Op>(s), s & 1, lo, hi, wall, g.chunk, k);
     __syncthreads();
   }
 };
@@ -402,6 +404,7 @@ __global__ void __launch_bounds__(1024) k_swept_persist(Geom g, typename Op::K k
 // ---------------------------------------------------------------------------
 template <typename T, class Op>
 struct ClusterCtx {
+  static constexpr int kR = Op::R, kC = Op::C;
   T* sm;         // the block's window rows (and Euler scratch)
   T* ex_in;      // export area of the previous pass (read remotely)
   T* ex_out;     // export area this pass writes (own tile's edges)
@@ -429,7 +432,7 @@ struct ClusterCtx {
     ex_out[e - (int64_t)my_rank * g.E] = row(r, c)[j];
   }
   __device__ __forceinline__ void level(int s, int, int lo, int hi, int64_t, int wall) {
-    LevelImpl<T, Op>::run(sm, g.M, stage_of(g, s), s & 1, lo, hi, wall, g.chunk, k);
+    LevelImpl<T, Op>::run(sm, g.M, stage_c<Op>(s), s & 1, lo, hi, wall, g.chunk, k);
     __syncthreads();
   }
 };
@@ -533,6 +536,7 @@ __device__ __forceinline__ void adjoint_level(T* sm, int M, int stage, int out_r
 
 template <typename T, class AOp>
 struct AdjCtx {
+  static constexpr int kR = AOp::R, kC = AOp::C;
   T* sm;
   Geom g;
   typename AOp::K k;
@@ -561,7 +565,7 @@ struct AdjCtx {
   __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) { e_out[e] = row(r, c)[j]; }
   __device__ __forceinline__ void level(int s, int b, int lo, int hi, int64_t origin, int wall) {
     const int64_t L = base + b + s;
-    adjoint_level<T, AOp>(sm, g.M, stage_of(g, s), s & 1, lo, hi, wall, origin, g.N, tape + (top - L) * g.N, k,
+    adjoint_level<T, AOp>(sm, g.M, stage_c<AOp>(s), s & 1, lo, hi, wall, origin, g.N, tape + (top - L) * g.N, k,
                           acc);
     __syncthreads();
   }

@@ -61,6 +61,24 @@ SW_HD int64_t wrap_n(int64_t x, int64_t n) {
 // stage (0-based) of the update that produces sub-timestep level s >= 1
 SW_HD int stage_of(const Geom& g, int s) { return (s - 1) % g.S; }
 
+// the same with the scheme's stage count Op::S as a compile-time constant
+template <class Op>
+SW_HD int stage_c(int s) {
+  return Op::S == 1 ? 0 : (s - 1) % Op::S;
+}
+
+// The geometry as a pass sees it in context Cx: the stencil radius and the
+// values per point replaced by the constants the context fixes at compile
+// time (Cx::kR, Cx::kC; 0 keeps the runtime field, as in the host checker),
+// so that on the device the index arithmetic of the phases folds to constants.
+template <class Cx>
+SW_HD Geom fixed_geom(const Geom& g) {
+  Geom f = g;
+  if (Cx::kR > 0) f.R = Cx::kR;
+  if (Cx::kC > 0) f.C = Cx::kC;
+  return f;
+}
+
 // tile tiers: level s on local [R + R s, W + R - R s)
 SW_HD int up_lo(const Geom& g, int s) { return g.R + g.R * s; }
 SW_HD int up_hi(const Geom& g, int s) { return g.W + g.R - g.R * s; }

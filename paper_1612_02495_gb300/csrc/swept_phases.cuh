@@ -25,11 +25,12 @@ namespace swept {
 // 2R edge values of tiers 0..hh-1 on both sides; with write_top, also write
 // tier hh (the trapezoid's top, non-empty when hh < h) back to u.
 template <class Cx>
-SW_HD void run_up(Cx& cx, const Geom& g, int64_t b, int hh, bool write_top) {
+SW_HD void run_up(Cx& cx, const Geom& g_in, int64_t b, int hh, bool write_top) {
+  const Geom g = fixed_geom<Cx>(g_in);
   const int64_t x0 = b * (int64_t)g.W;
   const int64_t origin = x0 - g.R;
   cx.for_range(0, g.W * g.C, [&](int i) {
-    const int c = i / g.W, k = i - c * g.W;
+    const int c = g.C == 1 ? 0 : i / g.W, k = i - c * g.W;
     cx.load_u(0, c, g.R + k, x0 + k);
   });
   cx.sync();
@@ -37,7 +38,7 @@ SW_HD void run_up(Cx& cx, const Geom& g, int64_t b, int hh, bool write_top) {
   const int per_level = g.C * 2 * g.R;
   const int per_side = hh * per_level;
   cx.for_range(0, 2 * per_side, [&](int i) {
-    const int side = i / per_side;
+    const int side = i >= per_side ? 1 : 0;
     const int rem = i - side * per_side;
     const int s = rem / per_level;
     const int c = (rem - s * per_level) / (2 * g.R);
@@ -48,7 +49,7 @@ SW_HD void run_up(Cx& cx, const Geom& g, int64_t b, int hh, bool write_top) {
     const int lo = up_lo(g, hh), w = up_hi(g, hh) - lo;
     if (w > 0)
       cx.for_range(0, w * g.C, [&](int i) {
-        const int c = i / w, k = i - c * w;
+        const int c = g.C == 1 ? 0 : i / w, k = i - c * w;
         cx.store_u(hh & 1, c, lo + k, origin + lo + k);
       });
   }
@@ -63,7 +64,8 @@ SW_HD void run_up(Cx& cx, const Geom& g, int64_t b, int hh, bool write_top) {
 //   MODE_GAP:     hh < h, write the grown gap [c - R hh, c + R hh) of tier hh
 //                 (completes the remainder trapezoids).
 template <class Cx>
-SW_HD void run_diamond(Cx& cx, const Geom& g, int64_t b, int odd, int mode, int hh) {
+SW_HD void run_diamond(Cx& cx, const Geom& g_in, int64_t b, int odd, int mode, int hh) {
+  const Geom g = fixed_geom<Cx>(g_in);
   const int64_t c = pass_center(g, odd, b);
   const int64_t origin = c - g.W / 2 - g.R;
   const int64_t tl = left_tile(g, odd, b);
@@ -71,7 +73,7 @@ SW_HD void run_diamond(Cx& cx, const Geom& g, int64_t b, int odd, int mode, int 
   const int per_level = g.C * 2 * g.R;
   const int per_side = hh * per_level;
   cx.for_range(0, 2 * per_side, [&](int i) {
-    const int which = i / per_side;  // 0: right edges of the left tile, 1: left edges of the right tile
+    const int which = i >= per_side ? 1 : 0;  // 0: right edges of the left tile, 1: left edges of the right tile
     const int rem = i - which * per_side;
     const int s = rem / per_level;
     const int cc = (rem - s * per_level) / (2 * g.R);
@@ -87,7 +89,7 @@ SW_HD void run_diamond(Cx& cx, const Geom& g, int64_t b, int odd, int mode, int 
     for (int s = 1; s < g.h; ++s) cx.level(s, g.h, up_lo(g, s), up_hi(g, s), origin, wall);
     const int per_side_h = g.h * per_level;
     cx.for_range(0, 2 * per_side_h, [&](int i) {
-      const int side = i / per_side_h;
+      const int side = i >= per_side_h ? 1 : 0;
       const int rem = i - side * per_side_h;
       const int s = rem / per_level;
       const int cc = (rem - s * per_level) / (2 * g.R);
@@ -96,13 +98,13 @@ SW_HD void run_diamond(Cx& cx, const Geom& g, int64_t b, int odd, int mode, int 
     });
   } else if (mode == MODE_DOWN) {
     cx.for_range(0, g.W * g.C, [&](int i) {
-      const int cc = i / g.W, k = i - cc * g.W;
+      const int cc = g.C == 1 ? 0 : i / g.W, k = i - cc * g.W;
       cx.store_u(g.h & 1, cc, g.R + k, origin + g.R + k);
     });
   } else {
     const int lo = grow_lo(g, hh), w = grow_hi(g, hh) - lo;
     cx.for_range(0, w * g.C, [&](int i) {
-      const int cc = i / w, k = i - cc * w;
+      const int cc = g.C == 1 ? 0 : i / w, k = i - cc * w;
       cx.store_u(hh & 1, cc, lo + k, origin + lo + k);
     });
   }
