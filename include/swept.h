@@ -89,6 +89,13 @@ typedef enum {
  *            thread-block cluster; each block keeps its tile in shared memory
  *            for the whole solve and reads its neighbour's edges through
  *            distributed shared memory, with a cluster barrier between passes
+ *   warp_tiles 1: heat and KS with tile_w = 32 P, P in {1, 2, 4, 8} (P >= 2 for
+ *            KS): each tile is one warp (threads must be 0 or 32) whose lane l
+ *            keeps points l P .. l P + P - 1 of the tier rows in registers and
+ *            reads its stencil neighbours from lanes l - 1 and l + 1 by warp
+ *            shuffle, so a tier needs no shared-memory access and no barrier.
+ *            Works with the per-pass, persistent and cluster modes; results are
+ *            bit-identical to the shared-memory tiers.
  * Stability (Fo <= 1/2, CFL) is the caller's responsibility and is not checked.
  */
 typedef struct {
@@ -105,7 +112,8 @@ typedef struct {
   int32_t chunk;    /* points per thread per trip: 1, 2 (strided pairs), 3, 5, 7, 9 (consecutive); 0 = 1 */
   int32_t persistent; /* 1: swept_step_n runs all passes in one persistent kernel */
   int32_t cluster;    /* 1: the whole grid (2..16 tiles) is one thread-block cluster */
-  int32_t reserved[3];
+  int32_t warp_tiles; /* 1: one warp per tile, tier rows in registers, neighbours by warp shuffle */
+  int32_t reserved[2];
 } swept_config;
 
 /* Plan chosen by swept_init (read-only report). */
@@ -122,7 +130,7 @@ typedef struct {
   int32_t chunk;           /* points per thread per tier */
   int32_t persistent;      /* 1: persistent kernel */
   int32_t cluster;         /* 1: single-cluster kernel */
-  int32_t reserved;
+  int32_t warp_tiles;      /* 1: tier rows in registers, one warp per tile */
 } swept_plan_info;
 
 typedef struct swept_handle swept_handle;

@@ -373,6 +373,21 @@ swept_status swept_init(const swept_config* cfg, swept_handle** out) {
     delete h;
     return SWEPT_EINVAL;
   }
+  // tiers in registers: one warp per tile, W / 32 points per lane
+  if (cfg->warp_tiles != 0 && cfg->warp_tiles != 1) {
+    delete h;
+    return SWEPT_EINVAL;
+  }
+  if (cfg->warp_tiles == 1) {
+    const int P = W / 32;
+    if (im->C != 1 || W % 32 != 0 || (P != 1 && P != 2 && P != 4 && P != 8) || P < R || g.chunk != 1 ||
+        (cfg->threads != 0 && cfg->threads != 32)) {
+      delete h;
+      return SWEPT_EINVAL;
+    }
+    g.P = P;
+    th = 32;
+  }
   h->threads = th;
   h->smem = (size_t)im->smem_values(g.M) * im->value_bytes;
   if (h->smem > (size_t)max_smem) {
@@ -440,7 +455,7 @@ swept_status swept_step_n(swept_handle* h, void* u_dev, int64_t nsteps, void* st
   }
   if (h->persistent) {
     if (!h->persist_blocks) {
-      const int per_sm = h->impl->persist_blocks_per_sm(h->threads, h->smem);
+      const int per_sm = h->impl->persist_blocks_per_sm(h->g.P, h->threads, h->smem);
       if (per_sm < 1) return fail(h, SWEPT_EINVAL, "persistent kernel does not fit on an SM");
       h->persist_blocks = per_sm * h->sm_count;
     }
@@ -653,7 +668,7 @@ swept_status swept_get_plan(const swept_handle* h, swept_plan_info* out) {
   out->chunk = h->g.chunk;
   out->persistent = h->persistent ? 1 : 0;
   out->cluster = h->cluster ? 1 : 0;
-  out->reserved = 0;
+  out->warp_tiles = h->g.P > 0 ? 1 : 0;
   return SWEPT_OK;
 }
 

@@ -2,6 +2,8 @@
 #pragma once
 #include <string.h>
 
+#include <type_traits>
+
 #include "impl.h"
 #include "kernels.cuh"
 
@@ -15,6 +17,21 @@ struct Launch {
     return kk;
   }
   static int64_t smem_values(int M) { return swept_smem_values<Op>(M); }
+  // register tiers exist for scalar schemes with at least R points per lane
+  static constexpr bool p_ok(int P) { return P == 0 || (Op::C == 1 && P >= Op::R); }
+  // fn(std::integral_constant<int, P>) for the kernel variant of g.P
+  template <class Fn>
+  static cudaError_t with_p(int P, Fn&& fn) {
+    switch (P) {
+      case 0: return fn(std::integral_constant<int, 0>{});
+      case 1: if constexpr (p_ok(1)) return fn(std::integral_constant<int, 1>{}); break;
+      case 2: if constexpr (p_ok(2)) return fn(std::integral_constant<int, 2>{}); break;
+      case 4: if constexpr (p_ok(4)) return fn(std::integral_constant<int, 4>{}); break;
+      case 8: if constexpr (p_ok(8)) return fn(std::integral_constant<int, 8>{}); break;
+      default: break;
+    }
+    return cudaErrorInvalidValue;
+  }
   static cudaError_t prepare(size_t bytes) {
     cudaError_t e = cudaFuncSetAttribute(k_swept_up<T, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
@@ -22,15 +39,21 @@ struct Launch {
   }
   static cudaError_t up(const Geom& g, const void* k, const void* u_in, void* u_out, void* e_out, int hh,
                         int write_top, int threads, size_t smem, cudaStream_t s) {
-    k_swept_up<T, Op><<<(unsigned)g.nt, threads, smem, s>>>(g, kc(k), (const T*)u_in, (T*)u_out, (T*)e_out, hh,
-                                                            write_top);
-    return cudaGetLastError();
+    return with_p(g.P, [&](auto pc) {
+      constexpr int P = decltype(pc)::value;
+      k_swept_up<T, Op, P><<<(unsigned)g.nt, threads, smem, s>>>(g, kc(k), (const T*)u_in, (T*)u_out, (T*)e_out, hh,
+                                                                 write_top);
+      return cudaGetLastError();
+    });
   }
   static cudaError_t diamond(const Geom& g, const void* k, void* u_out, const void* e_in, void* e_out, int odd,
                              int mode, int hh, int threads, size_t smem, cudaStream_t s) {
-    k_swept_diamond<T, Op><<<(unsigned)g.nt, threads, smem, s>>>(g, kc(k), (T*)u_out, (const T*)e_in, (T*)e_out, odd,
-                                                                 mode, hh);
-    return cudaGetLastError();
+    return with_p(g.P, [&](auto pc) {
+      constexpr int P = decltype(pc)::value;
+      k_swept_diamond<T, Op, P><<<(unsigned)g.nt, threads, smem, s>>>(g, kc(k), (T*)u_out, (const T*)e_in,
+                                                                      (T*)e_out, odd, mode, hh);
+      return cudaGetLastError();
+    });
   }
   static cudaError_t classic(const Geom& g, const void* k, int stage, const void* in, void* out, cudaStream_t s) {
     const int B = 256;
@@ -48,31 +71,42 @@ struct Launch {
   static cudaError_t persist(const Geom& g, const void* k, void* u, void* e0, void* e1, int64_t n_sub, int* done,
                              unsigned long long* queue, int* error, uint32_t spin_limit, int blocks, int threads,
                              size_t smem, cudaStream_t s) {
-    if (smem > 48 * 1024) {
-      cudaError_t e =
-          cudaFuncSetAttribute(k_swept_persist<T, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
-    PersistCtl c{done, queue, error, spin_limit};
-    k_swept_persist<T, Op><<<blocks, threads, smem, s>>>(g, kc(k), (T*)u, (T*)e0, (T*)e1, n_sub, c);
-    return cudaGetLastError();
+    return with_p(g.P, [&](auto pc) {
+      constexpr int P = decltype(pc)::value;
+      if (smem > 48 * 1024) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_swept_persist<T, Op, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+      }
+      PersistCtl c{done, queue, error, spin_limit};
+      k_swept_persist<T, Op, P><<<blocks, threads, smem, s>>>(g, kc(k), (T*)u, (T*)e0, (T*)e1, n_sub, c);
+      return cudaGetLastError();
+    });
   }
-  static int persist_blocks_per_sm(int threads, size_t smem) {
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k_swept_persist<T, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
-      return 0;
+  static int persist_blocks_per_sm(int P_, int threads, size_t smem) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_swept_persist<T, Op>, threads, smem) != cudaSuccess)
-      return 0;
-    return n;
+    const cudaError_t e = with_p(P_, [&](auto pc) {
+      constexpr int P = decltype(pc)::value;
+      if (smem > 48 * 1024) {
+        cudaError_t e2 =
+            cudaFuncSetAttribute(k_swept_persist<T, Op, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e2 != cudaSuccess) return e2;
+      }
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_swept_persist<T, Op, P>, threads, smem);
+    });
+    return e == cudaSuccess ? n : 0;
   }
   // smem = window bytes; the two export areas (2 E values) are added here
   static cudaError_t cluster(const Geom& g, const void* k, void* u, int64_t n_sub, int threads, size_t smem,
                              cudaStream_t s) {
+    return with_p(g.P, [&](auto pc) { return cluster_p<decltype(pc)::value>(g, k, u, n_sub, threads, smem, s); });
+  }
+  template <int P>
+  static cudaError_t cluster_p(const Geom& g, const void* k, void* u, int64_t n_sub, int threads, size_t smem,
+                               cudaStream_t s) {
     const int64_t win_values = (int64_t)(smem / sizeof(T));
     const size_t bytes = smem + 2 * (size_t)g.E * sizeof(T);
-    auto fn = k_swept_cluster<T, Op>;
+    auto fn = k_swept_cluster<T, Op, P>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e == cudaSuccess && bytes > 48 * 1024)
       e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);

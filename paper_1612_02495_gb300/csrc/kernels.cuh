@@ -239,6 +239,8 @@ struct Tape {
 
 template <typename T, class Op, bool TAPE = false>
 struct DevCtx {
+  using value_type = T;
+  using op_type = Op;
   static constexpr int kR = Op::R, kC = Op::C;
   T* sm;
   Geom g;
@@ -279,6 +281,137 @@ struct DevCtx {
   }
 };
 
+
+// ---------------------------------------------------------------------------
+// Tiers in registers (scalar schemes, Geom::P > 0): the block is one warp and
+// owns one tile of W = 32 P points.  Lane l keeps window points R + l P + i
+// (i < P) of both tier rows in registers; the halo points [0, R) and
+// [W + R, W + 2R), which only ever hold inserted edges, are kept by every lane
+// and used by lanes 0 and 31.  A tier takes the R points beyond each end of a
+// lane's run from the neighbouring lanes with __shfl_up_sync/__shfl_down_sync,
+// so it costs no shared-memory access and no barrier.  The loads and stores
+// of a pass (tile, edges) still go through the shared-memory rows of the base
+// context: the rows move into registers at the first tier of a pass and back
+// (then __syncwarp) before the first load/store loop after the tiers.  Every
+// tier evaluates the same Op::point on the same operands in the same order as
+// the shared-memory tiers, so the two give identical results.
+// ---------------------------------------------------------------------------
+template <class Base, int P>
+struct RegCtx : Base {
+  using T = typename Base::value_type;
+  using Op = typename Base::op_type;
+  static constexpr int R = Op::R;
+  static_assert(Op::C == 1 && P >= R, "register tiers need a scalar scheme and at least R points per lane");
+  T a[P], b[P];            // rows 0 (even tiers) and 1 (odd tiers)
+  T ha[2 * R], hb[2 * R];  // halo of rows 0 / 1: [0, R) -> points 0..R-1, [R, 2R) -> points W+R..W+2R-1
+  bool in_regs;
+
+  __device__ __forceinline__ explicit RegCtx(const Base& base) : Base(base), in_regs(false) {}
+
+  __device__ __forceinline__ static int lane() { return (int)(threadIdx.x & 31u); }
+  __device__ __forceinline__ void fill() {
+    const T* r0 = this->row(0, 0);
+    const T* r1 = this->row(1, 0);
+    const int p0 = R + lane() * P;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      a[i] = r0[p0 + i];
+      b[i] = r1[p0 + i];
+    }
+    const int W = this->g.W;
+#pragma unroll
+    for (int d = 0; d < R; ++d) {
+      ha[d] = r0[d];
+      hb[d] = r1[d];
+      ha[R + d] = r0[W + R + d];
+      hb[R + d] = r1[W + R + d];
+    }
+    in_regs = true;
+  }
+  __device__ __forceinline__ void spill() {
+    T* r0 = this->row(0, 0);
+    T* r1 = this->row(1, 0);
+    const int p0 = R + lane() * P;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+      r0[p0 + i] = a[i];
+      r1[p0 + i] = b[i];
+    }
+    __syncwarp();
+    in_regs = false;
+  }
+  template <class F>
+  __device__ __forceinline__ void for_range(int lo, int hi, F&& f) {
+    if (in_regs) spill();
+    Base::for_range(lo, hi, f);
+  }
+  // tier s on [lo, hi): into row s&1 from row (s-1)&1; stage (s-1) mod S
+  __device__ __forceinline__ void level(int s, int, int lo, int hi, int64_t, int wall) {
+    if (!in_regs) fill();
+    if (s & 1)
+      tier<0>(a, ha, b, lo, hi, wall);
+    else
+      tier<Op::S == 1 ? 0 : 1>(b, hb, a, lo, hi, wall);
+  }
+  template <int STAGE>
+  __device__ __forceinline__ void tier(const T (&src)[P], const T (&hs)[2 * R], T (&dst)[P], int lo, int hi,
+                                       int wall) {
+    const int ln = lane();
+    T w[P + 2 * R];  // points p0 - R .. p0 + P + R - 1 of the source tier
+#pragma unroll
+    for (int d = 0; d < R; ++d) {
+      const T x = __shfl_up_sync(0xffffffffu, src[P - R + d], 1);
+      w[d] = ln == 0 ? hs[d] : x;
+      const T y = __shfl_down_sync(0xffffffffu, src[d], 1);
+      w[R + P + d] = ln == 31 ? hs[R + d] : y;
+    }
+#pragma unroll
+    for (int i = 0; i < P; ++i) w[R + i] = src[i];
+    const int p0 = R + ln * P;
+    if (wall == NO_WALL) {
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        const T r = Op::template point<STAGE>(&w[i], dst[i], this->k);
+        if (p0 + i >= lo && p0 + i < hi) dst[i] = r;
+      }
+    } else {
+      // across a mirror wall the neighbour read is the mirror image, which
+      // lies within R of the point on its own side (nbr), i.e. inside w
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        T v[2 * R + 1];
+#pragma unroll
+        for (int d = 0; d <= 2 * R; ++d) {
+          const int q = nbr(p0 + i, d - R, wall) - (p0 + i);
+          T x = w[i + R];
+#pragma unroll
+          for (int e = 0; e <= 2 * R; ++e)
+            if (q == e - R) x = w[i + e];
+          v[d] = x;
+        }
+        const T r = Op::template point<STAGE>(v, dst[i], this->k);
+        if (p0 + i >= lo && p0 + i < hi) dst[i] = r;
+      }
+    }
+  }
+};
+
+// the context of a pass: Base itself (P = 0) or Base with its tiers in registers.
+// The register-tier kernels run one warp per block and are compiled for 16
+// co-resident blocks per SM (at most 128 registers per thread).
+template <class Base, int P>
+struct WithTiers {
+  using type = RegCtx<Base, P>;
+};
+template <class Base>
+struct WithTiers<Base, 0> {
+  using type = Base;
+};
+template <int P, class Base>
+__device__ __forceinline__ typename WithTiers<Base, P>::type tiers_ctx(const Base& base) {
+  return typename WithTiers<Base, P>::type(base);
+}
+
 // ---------------------------------------------------------------------------
 // persistent single-problem swept kernel: the launch sequence of
 // for_each_launch as one queue of (pass k, tile b) items, item = k * nt + b,
@@ -298,6 +431,8 @@ struct PersistCtl {
 
 template <typename T, class Op>
 struct PDevCtx {
+  using value_type = T;
+  using op_type = Op;
   static constexpr int kR = Op::R, kC = Op::C;
   T* sm;
   Geom g;
@@ -334,8 +469,8 @@ __device__ __forceinline__ bool persist_wait(const int* flag, int need, const Pe
   }
 }
 
-template <typename T, class Op>
-__global__ void __launch_bounds__(1024) k_swept_persist(Geom g, typename Op::K k, T* u, T* e0, T* e1, int64_t n_sub,
+template <typename T, class Op, int P = 0>
+__global__ void __launch_bounds__(P > 0 ? 32 : 1024, P > 0 ? 16 : 1) k_swept_persist(Geom g, typename Op::K k, T* u, T* e0, T* e1, int64_t n_sub,
                                                         PersistCtl ctl) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int64_t s_item;
@@ -369,7 +504,7 @@ __global__ void __launch_bounds__(1024) k_swept_persist(Geom g, typename Op::K k
     }
     __syncthreads();
     if (!s_ok) break;
-    PDevCtx<T, Op> cx{reinterpret_cast<T*>(smraw), g, k, u, nullptr, nullptr};
+    auto cx = tiers_ctx<P>(PDevCtx<T, Op>{reinterpret_cast<T*>(smraw), g, k, u, nullptr, nullptr});
     if (kp < main_passes) {
       if (kp == 0) {
         cx.e_out = eb[0];
@@ -404,6 +539,8 @@ __global__ void __launch_bounds__(1024) k_swept_persist(Geom g, typename Op::K k
 // ---------------------------------------------------------------------------
 template <typename T, class Op>
 struct ClusterCtx {
+  using value_type = T;
+  using op_type = Op;
   static constexpr int kR = Op::R, kC = Op::C;
   T* sm;         // the block's window rows (and Euler scratch)
   T* ex_in;      // export area of the previous pass (read remotely)
@@ -437,8 +574,8 @@ struct ClusterCtx {
   }
 };
 
-template <typename T, class Op>
-__global__ void __launch_bounds__(1024) k_swept_cluster(Geom g, typename Op::K k, T* u, int64_t n_sub,
+template <typename T, class Op, int P = 0>
+__global__ void __launch_bounds__(P > 0 ? 32 : 1024, P > 0 ? 16 : 1) k_swept_cluster(Geom g, typename Op::K k, T* u, int64_t n_sub,
                                                         int64_t smem_values) {
   extern __shared__ __align__(16) unsigned char smraw[];
   namespace cg = cooperative_groups;
@@ -446,7 +583,7 @@ __global__ void __launch_bounds__(1024) k_swept_cluster(Geom g, typename Op::K k
   T* sm = reinterpret_cast<T*>(smraw);
   T* ex[2] = {sm + smem_values, sm + smem_values + g.E};
   const unsigned b = cluster.block_rank();
-  ClusterCtx<T, Op> cx{sm, ex[1], ex[0], g, k, u, b};
+  auto cx = tiers_ctx<P>(ClusterCtx<T, Op>{sm, ex[1], ex[0], g, k, u, b});
   const int q = (int)(n_sub / g.h), rem = (int)(n_sub % g.h);
   if (q > 0) {
     cx.ex_out = ex[0];
@@ -475,19 +612,19 @@ static __global__ void k_latch_error(const int* err, int* status) {
   if (threadIdx.x == 0 && blockIdx.x == 0 && *err != 0 && *status == 0) *status = *err;
 }
 
-template <typename T, class Op>
-__global__ void __launch_bounds__(1024) k_swept_up(Geom g, typename Op::K k, const T* u_in, T* u_out, T* e_out,
+template <typename T, class Op, int P = 0>
+__global__ void __launch_bounds__(P > 0 ? 32 : 1024, P > 0 ? 16 : 1) k_swept_up(Geom g, typename Op::K k, const T* u_in, T* u_out, T* e_out,
                                                    int hh, int write_top) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  DevCtx<T, Op> cx{reinterpret_cast<T*>(smraw), g, k, u_in, u_out, nullptr, e_out, Tape<T>{}};
+  auto cx = tiers_ctx<P>(DevCtx<T, Op>{reinterpret_cast<T*>(smraw), g, k, u_in, u_out, nullptr, e_out, Tape<T>{}});
   run_up(cx, g, (int64_t)blockIdx.x, hh, write_top != 0);
 }
 
-template <typename T, class Op>
-__global__ void __launch_bounds__(1024) k_swept_diamond(Geom g, typename Op::K k, T* u_out, const T* e_in, T* e_out,
+template <typename T, class Op, int P = 0>
+__global__ void __launch_bounds__(P > 0 ? 32 : 1024, P > 0 ? 16 : 1) k_swept_diamond(Geom g, typename Op::K k, T* u_out, const T* e_in, T* e_out,
                                                         int odd, int mode, int hh) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  DevCtx<T, Op> cx{reinterpret_cast<T*>(smraw), g, k, nullptr, u_out, e_in, e_out, Tape<T>{}};
+  auto cx = tiers_ctx<P>(DevCtx<T, Op>{reinterpret_cast<T*>(smraw), g, k, nullptr, u_out, e_in, e_out, Tape<T>{}});
   run_diamond(cx, g, (int64_t)blockIdx.x, odd, mode, hh);
 }
 

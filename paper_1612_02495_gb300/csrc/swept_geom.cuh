@@ -46,6 +46,7 @@ struct Geom {
   int E;       // values per tile in an edge buffer: 2 sides * h * C * 2R
   int bc;      // 0 periodic, 1 mirror walls at -1/2 and N-1/2
   int chunk;   // consecutive points one thread advances per tier (1 = strided mapping)
+  int P = 0;   // tiers in registers: points per lane of the one warp that owns a tile (0 = in shared memory)
 };
 
 SW_HD int64_t floor_div(int64_t a, int64_t b) {

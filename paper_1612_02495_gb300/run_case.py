@@ -1,7 +1,7 @@
 """Run one solve of a configuration through the C ABI and print its time.
 
   python -m paper_1612_02495_gb300.run_case --scheme ks --dtype f64 --n 1048576 \\
-      --nsteps 600 [--path swept|classic] [--tile 0] [--threads 0] [--chunk 0] [--persistent 0] [--cluster 0] [--repeat 1]
+      --nsteps 600 [--path swept|classic] [--tile 0] [--threads 0] [--chunk 0] [--persistent 0] [--cluster 0] [--warp-tiles 0] [--repeat 1]
 
 Used to profile a single kernel on a chosen size (e.g. under ncu).  One
 untimed warm-up solve precedes the timed repeats.
@@ -25,6 +25,7 @@ def main(argv=None):
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--persistent", type=int, default=0)
     ap.add_argument("--cluster", type=int, default=0)
+    ap.add_argument("--warp-tiles", type=int, default=0)
     ap.add_argument("--repeat", type=int, default=1)
     a = ap.parse_args(argv)
 
@@ -48,7 +49,7 @@ def main(argv=None):
         args = (S.EULER, dt_code, a.n, p["dx"], p["dt"], p["gamma"], S.BC_REFLECTIVE)
         u0 = p["U0"]
     sol = S.Solver(*args, tile_w=a.tile, threads=a.threads, chunk=a.chunk, persistent=a.persistent,
-                   cluster=a.cluster)
+                   cluster=a.cluster, warp_tiles=a.warp_tiles)
     u_init = torch.from_numpy(np.ascontiguousarray(u0)).cuda()
     u = u_init.clone()
     run = sol.step if a.path == "swept" else sol.classic

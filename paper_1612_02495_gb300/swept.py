@@ -36,7 +36,7 @@ class swept_config(ctypes.Structure):
                 ("reserved0", ctypes.c_int32), ("n", ctypes.c_int64), ("dx", ctypes.c_double),
                 ("dt", ctypes.c_double), ("param", ctypes.c_double * 4), ("tile_w", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("chunk", ctypes.c_int32), ("persistent", ctypes.c_int32),
-                ("cluster", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("cluster", ctypes.c_int32), ("warp_tiles", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class swept_plan_info(ctypes.Structure):
@@ -44,7 +44,7 @@ class swept_plan_info(ctypes.Structure):
                 ("radius", ctypes.c_int32), ("stages", ctypes.c_int32), ("components", ctypes.c_int32),
                 ("tiles", ctypes.c_int64), ("smem_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
                 ("chunk", ctypes.c_int32), ("persistent", ctypes.c_int32), ("cluster", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("warp_tiles", ctypes.c_int32)]
 
 
 _H = ctypes.c_void_p
@@ -117,13 +117,14 @@ def check(status, h=None, what=""):
 
 
 def make_config(scheme, dtype, n, dx, dt, param0, bc=BC_PERIODIC, tile_w=0, threads=0, chunk=0, persistent=0,
-                cluster=0):
+                cluster=0, warp_tiles=0):
     c = swept_config()
     c.scheme, c.dtype, c.bc, c.n = int(scheme), int(dtype), int(bc), int(n)
     c.dx, c.dt = float(dx), float(dt)
     c.param[0] = float(param0)
     c.tile_w, c.threads, c.chunk, c.persistent = int(tile_w), int(threads), int(chunk), int(persistent)
     c.cluster = int(cluster)
+    c.warp_tiles = int(warp_tiles)
     return c
 
 
@@ -164,10 +165,11 @@ class Solver:
     """
 
     def __init__(self, scheme, dtype, n, dx, dt, param0, bc=BC_PERIODIC, tile_w=0, threads=0, chunk=0, persistent=0,
-                 cluster=0):
+                 cluster=0, warp_tiles=0):
         import torch
 
-        self.cfg = make_config(scheme, dtype, n, dx, dt, param0, bc, tile_w, threads, chunk, persistent, cluster)
+        self.cfg = make_config(scheme, dtype, n, dx, dt, param0, bc, tile_w, threads, chunk, persistent, cluster,
+                               warp_tiles)
         self.h = init(self.cfg)
         self.scheme, self.dtype, self.n = scheme, dtype, n
         self.torch_dtype = torch.float32 if dtype == F32 else torch.float64

@@ -53,8 +53,14 @@ def cfg(S, scheme=None, **kw):
     dict(n=0), dict(n=-5), dict(dx=0.0), dict(dt=-1.0), dict(tile_w=12), dict(tile_w=4096),
     dict(tile_w=1000), dict(threads=48), dict(threads=2048), dict(dtype=7), dict(scheme=9),
     dict(bc=1),  # KS is periodic only
+    dict(warp_tiles=2), dict(warp_tiles=1, tile_w=32),  # KS needs at least 2 points per lane
+    dict(warp_tiles=1, tile_w=96), dict(warp_tiles=1, tile_w=512),  # W / 32 must be 1, 2, 4 or 8
+    dict(warp_tiles=1, tile_w=64, threads=64), dict(warp_tiles=1, tile_w=64, chunk=3),
+    dict(warp_tiles=1, scheme=2, tile_w=64, param0=1.4, bc=1),  # Euler keeps its tiers in shared memory
 ])
 def test_init_rejects_invalid_configs(S, bad):
+    if bad.get("scheme") == 2:
+        bad = dict(bad, scheme=S.EULER)
     c = cfg(S, **bad)
     h = ctypes.c_void_p()
     assert S.swept_init(ctypes.byref(c), ctypes.byref(h)) == S.SWEPT_EINVAL
@@ -180,3 +186,16 @@ def test_autotune_tile_candidates(S):
     # a non-power-of-two size keeps its legal divisors (multiples of 4r, >= 2 tiles)
     c = autotune.tile_candidates(S.KS, 3 * 1000)
     assert c and all(3000 % w == 0 and w % 8 == 0 and 3000 // w >= 2 for w in c)
+
+
+@pytest.mark.parametrize("scheme,W", [("heat", 32), ("heat", 64), ("heat", 256), ("ks", 64), ("ks", 128), ("ks", 256)])
+def test_warp_tiles_plan(S, scheme, W):
+    sc = S.HEAT if scheme == "heat" else S.KS
+    c = cfg(S, scheme=sc, n=8 * W, tile_w=W, warp_tiles=1)
+    h = ctypes.c_void_p()
+    assert S.swept_init(ctypes.byref(c), ctypes.byref(h)) == S.SWEPT_OK
+    p = S.plan(h.value)
+    assert p["warp_tiles"] == 1 and p["threads"] == 32 and p["tile_w"] == W
+    # the schedule itself is unchanged: the host replay still covers every point once
+    assert S.check_schedule(h.value, 3 * W + 5) == 8 * W * (3 * W + 5) * (1 if scheme == "heat" else 2)
+    S.swept_free(h.value)

@@ -347,3 +347,54 @@ def test_cluster_mode_parity(S, scheme, dtype, n, W, threads, nsteps, bc):
 def test_cluster_mode_rejects_more_than_16_tiles(S):
     with pytest.raises(S.SweptError):
         S.Solver(S.KS, S.F64, 17 * 64, 0.785, 0.005, 1.0, tile_w=64, cluster=1)
+
+
+WARP_CASES = [
+    # scheme, dtype, n, W (= 32 P), nsteps, bc, mode (0 per pass, 1 persistent, 2 cluster)
+    ("heat", np.float64, 1024, 64, 10000, 0, 0),   # the heat workload, P = 2
+    ("heat", np.float32, 1024, 64, 10000, 0, 0),
+    ("heat", np.float64, 7 * 32, 32, 333, 1, 0),   # P = 1, insulated ends, remainder
+    ("heat", np.float32, 5 * 128, 128, 1001, 1, 1),
+    ("heat", np.float64, 3 * 256, 256, 700, 0, 2),  # P = 8 in one cluster of 3
+    ("heat", np.float32, 16 * 64, 64, 2049, 1, 2),
+    ("ks", np.float64, 1 << 14, 64, 1001, 0, 0),   # P = 2
+    ("ks", np.float32, 1 << 14, 128, 2000, 0, 0),  # P = 4
+    ("ks", np.float64, 1 << 14, 256, 999, 0, 1),   # P = 8 persistent
+    ("ks", np.float32, 12 * 64, 64, 77, 0, 1),
+    ("ks", np.float64, 16 * 128, 128, 555, 0, 2),
+    ("ks", np.float64, 2 * 64, 64, 7, 0, 0),       # two tiles, remainder only
+]
+
+
+@pytest.mark.parametrize("scheme,dtype,n,W,nsteps,bc,mode", WARP_CASES)
+def test_warp_tiles_parity(S, scheme, dtype, n, W, nsteps, bc, mode):
+    """Tier rows in registers with warp-shuffle neighbour reads: equal to the
+    shared-memory swept path, classic and the oracle bit for bit."""
+    import torch
+
+    code = S.F64 if dtype == np.float64 else S.F32
+    if scheme == "heat":
+        p = inputs.heat_problem(n=n, dtype=dtype)
+        args, sc = (p["dx"], p["dt"], p["alpha"]), S.HEAT
+        ref = oracle.heat(p["u0"], p["dx"], p["dt"], p["alpha"], nsteps, bc=bc)
+    else:
+        p = inputs.ks_problem(n=n, dtype=dtype)
+        args, sc = (p["dx"], p["dt"], p["nu"]), S.KS
+        ref = oracle.ks(p["u0"], p["dx"], p["dt"], p["nu"], nsteps, threads=THREADS)
+    sol = S.Solver(sc, code, n, *args, bc=bc, tile_w=W, warp_tiles=1, persistent=int(mode == 1),
+                   cluster=int(mode == 2))
+    assert sol.plan["warp_tiles"] == 1 and sol.plan["threads"] == 32
+    smem = S.Solver(sc, code, n, *args, bc=bc, tile_w=W)
+    u = torch.from_numpy(p["u0"]).cuda()
+    v, w = u.clone(), u.clone()
+    sol.step(u, nsteps)
+    smem.step(v, nsteps)
+    sol.classic(w, nsteps)
+    torch.cuda.synchronize()
+    sol.sync_status()
+    got = u.cpu().numpy()
+    assert np.array_equal(got, v.cpu().numpy())
+    assert np.array_equal(got, w.cpu().numpy())
+    assert np.array_equal(got, ref)
+    sol.close()
+    smem.close()
