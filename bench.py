@@ -200,8 +200,7 @@ def measure_fp32(S, inputs, autotune, torch, stream, barrier, ws):
     """The same KS workload (N=2^20, 50,000 steps) in FP32: swept vs classic."""
     p = inputs.ks_problem(n=N, dtype=np.float32)
     t = autotune.tune_single(S.KS, S.F32, N, probe_steps=8000)
-    sol = S.Solver(S.KS, S.F32, N, p["dx"], p["dt"], p["nu"], tile_w=t["tile_w"], threads=t["threads"],
-                   persistent=t.get("persistent", 0), cluster=t.get("cluster", 0))
+    sol = autotune.solver_from_plan(S.KS, S.F32, N, p["dx"], p["dt"], p["nu"], t)
     u0 = torch.from_numpy(p["u0"]).cuda()
     u = u0.clone()
     res = {}
@@ -218,7 +217,7 @@ def measure_fp32(S, inputs, autotune, torch, stream, barrier, ws):
     sol.sync_status()
     sol.close()
     return {"workload": "KS N=2^20 FP32, 50,000 steps", "tile_w": t["tile_w"], "threads": t["threads"],
-            "persistent": t.get("persistent", 0),
+            "plan": {k: t.get(k, 0) for k in ("tile_w", "threads", "warp_tiles", "persistent", "cluster")},
             "swept_ms": res["swept"], "classic_ms": res["classic"],
             "swept_value": ws * N * NSTEPS / (res["swept"] * 1e-3),
             "classic_value": ws * N * NSTEPS / (res["classic"] * 1e-3),
@@ -254,6 +253,56 @@ def measure_batch(S, inputs, autotune, torch, stream, barrier, ws, with_f64):
         b.close()
         del u, u0
         torch.cuda.empty_cache()
+    return out
+
+
+# swept (tuned plan) vs classic across the paper's sizes; (label, scheme, dtype, n, steps, tuner probe steps)
+SIZE_CASES = [
+    ("heat N=2^10 FP64 periodic, 10,000 steps", "heat", "f64", 1 << 10, 10000, 2000),
+    ("heat N=2^10 FP32 periodic, 10,000 steps", "heat", "f32", 1 << 10, 10000, 2000),
+    ("KS N=2^14 FP64, 5,000 steps", "ks", "f64", 1 << 14, 5000, 1000),
+    ("KS N=2^14 FP32, 5,000 steps", "ks", "f32", 1 << 14, 5000, 1000),
+    ("KS N=2^16 FP64, 5,000 steps", "ks", "f64", 1 << 16, 5000, 1000),
+    ("KS N=2^16 FP32, 5,000 steps", "ks", "f32", 1 << 16, 5000, 1000),
+    ("KS N=2^18 FP64, 2,000 steps", "ks", "f64", 1 << 18, 2000, 1000),
+    ("KS N=2^18 FP32, 2,000 steps", "ks", "f32", 1 << 18, 2000, 1000),
+    ("Euler Sod N=2^16 FP64 reflective, 300 steps", "euler", "f64", 1 << 16, 300, 200),
+    ("Euler Sod N=2^20 FP64 reflective, 100 steps", "euler", "f64", 1 << 20, 100, 100),
+]
+
+
+def measure_sizes(S, autotune, torch, stream, barrier, ws, flush):
+    """Each SIZE_CASES workload with its autotuned swept plan and with the
+    classic path (CUDA events on the launching stream, L2 flushed before each
+    timed solve, best of three)."""
+    codes = {"heat": S.HEAT, "ks": S.KS, "euler": S.EULER}
+    out = []
+    for label, scheme, dt, n, nsteps, probe in SIZE_CASES:
+        sc, code = codes[scheme], (S.F64 if dt == "f64" else S.F32)
+        u0, args, bc = autotune.problem(sc, code, n)
+        plan = autotune.tune_single(sc, code, n, probe_steps=probe)
+        sol = autotune.solver_from_plan(sc, code, n, *args, plan, bc=bc)
+        d0 = torch.from_numpy(np.ascontiguousarray(u0)).cuda()
+        u = d0.clone()
+        res = {}
+        for name, fn in (("swept", sol.step), ("classic", sol.classic)):
+            fn(u, nsteps)
+            best = None
+            for _ in range(3):
+                u.copy_(d0)
+                flush.zero_()
+                ev = _event_time(torch, stream, lambda: fn(u, nsteps))
+                barrier()
+                t = ev[0].elapsed_time(ev[1])
+                best = t if best is None else min(best, t)
+            res[name] = best
+        sol.sync_status()
+        sol.close()
+        out.append({"workload": label, "swept_ms": res["swept"], "classic_ms": res["classic"],
+                    "speedup_vs_classic": res["classic"] / res["swept"],
+                    "swept_value": ws * n * nsteps / (res["swept"] * 1e-3),
+                    "classic_value": ws * n * nsteps / (res["classic"] * 1e-3),
+                    "plan": {k: plan.get(k, 0) for k in ("tile_w", "threads", "warp_tiles", "persistent", "cluster")}})
     return out
 
 
@@ -298,6 +347,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-sizes", action="store_true")
     ap.add_argument("--batch-f64", action="store_true", help="also time the FP64 batch (about 50 s)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -322,8 +372,7 @@ def main():
 
     p = inputs.ks_problem(n=N, seed=1 + rank)
     tuned = autotune.tune_single(S.KS, S.F64, N, probe_steps=4000)
-    sol = S.Solver(S.KS, S.F64, N, p["dx"], p["dt"], p["nu"], tile_w=tuned["tile_w"], threads=tuned["threads"],
-                   persistent=tuned.get("persistent", 0), cluster=tuned.get("cluster", 0))
+    sol = autotune.solver_from_plan(S.KS, S.F64, N, p["dx"], p["dt"], p["nu"], tuned)
     plan = sol.plan
     stream = torch.cuda.current_stream()
     u0 = torch.from_numpy(p["u0"]).cuda()
@@ -388,7 +437,8 @@ def main():
         units = N * 2 * NSTEPS
         roofline = {"bound": "alu", "achieved": FP64_FLOPS_PER_SUBSTEP * units / (ms * 1e-3) / 1e12,
                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": PERSIST_TRAFFIC_BYTES,
-                    "kernel": "k_swept_persist<double, KsOp<double>>", "peak_source": peak_src,
+                    "kernel": "k_swept_persist<double, KsOp<double>%s>" % (
+                        ", %d" % (plan["tile_w"] // 32) if plan.get("warp_tiles") else ""), "peak_source": peak_src,
                     "pipe_frac": FP64_INSTR_PER_SUBSTEP * units / (ms * 1e-3) / FP64_INSTR_PEAK,
                     "frac_of_measured_mix_ceiling": FP64_INSTR_PER_SUBSTEP * units / (ms * 1e-3) / FP64_KS_MIX_CEILING,
                     "kernel_ms_avg": ms, "kernel_share": 1.0}
@@ -404,7 +454,8 @@ def main():
         achieved = flops_per_diamond / (d_avg * 1e-3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": DIAMOND_TRAFFIC_BYTES,
-                    "kernel": "k_swept_diamond<double, KsOp<double>>", "peak_source": peak_src,
+                    "kernel": "k_swept_diamond<double, KsOp<double>%s>" % (
+                        ", %d" % (plan["tile_w"] // 32) if plan.get("warp_tiles") else ""), "peak_source": peak_src,
                     "pipe_frac": (FP64_INSTR_PER_SUBSTEP * N * plan["half_cycle"] / (d_avg * 1e-3)) / FP64_INSTR_PEAK,
                     "frac_of_measured_mix_ceiling": (FP64_INSTR_PER_SUBSTEP * N * plan["half_cycle"] / (d_avg * 1e-3))
                     / FP64_KS_MIX_CEILING,
@@ -418,6 +469,9 @@ def main():
     fp32 = None
     if not args.no_fp32:
         fp32 = measure_fp32(S, inputs, autotune, torch, stream, barrier, ws)
+    sizes = None
+    if not args.no_sizes:
+        sizes = measure_sizes(S, autotune, torch, stream, barrier, ws, flush)
     batched = None
     if not args.no_batch:
         batched = measure_batch(S, inputs, autotune, torch, stream, barrier, ws, args.batch_f64)
@@ -438,8 +492,10 @@ def main():
         out["fp32"] = fp32
     if batched:
         out["batched"] = batched
-    out["config"]["autotuned"] = {"tile_w": tuned["tile_w"], "threads": tuned["threads"],
-                                  "persistent": tuned.get("persistent", 0)}
+    if sizes:
+        out["sizes"] = sizes
+    out["config"]["autotuned"] = {k: tuned.get(k, 0) for k in ("tile_w", "threads", "warp_tiles", "persistent",
+                                                                "cluster")}
     if ms_classic:
         out["classic"] = {"value": ws * N * NSTEPS / (ms_classic * 1e-3), "ms_per_step": ms_classic}
         out["speedup_vs_classic"] = ms_classic / ms

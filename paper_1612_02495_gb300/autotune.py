@@ -6,7 +6,7 @@ best per problem size (Section "Results").  This tuner does the same on the
 GPU at hand, by timing short probes of the real kernels with CUDA events,
 and caches the winners in a JSON file keyed by device, scheme, dtype and size.
 
-  tune_single(scheme, dtype, n, ...)  -> {"tile_w", "threads", "ms"} for swept_step_n
+  tune_single(scheme, dtype, n, ...)  -> {"tile_w", "threads", "warp_tiles", "persistent", "cluster", "ms"}
   tune_batch(problems, dtype, ...)    -> {"tile_w", "threads", "ms"} for one batch plan
 
 Both only launch the library's kernels through the C ABI.
@@ -66,7 +66,9 @@ def _store(path, table):
         pass
 
 
-def _problem(scheme, dtype, n):
+def problem(scheme, dtype, n):
+    """Seeded initial state, (dx, dt, param) and boundary condition of the
+    workload the tuner probes (the same recipe the tests and the bench use)."""
     npd = np.float64 if dtype == S.F64 else np.float32
     if scheme == S.KS:
         p = inputs.ks_problem(n=n, dtype=npd)
@@ -95,46 +97,63 @@ def _time(fn, reps):
     return best
 
 
+def warp_tile_ok(scheme, W):
+    """Tile widths the register (warp-tile) mapping supports: W = 32 P with
+    P in {1, 2, 4, 8} and at least r points per lane; heat and KS only."""
+    P = W // 32
+    return scheme != S.EULER and W % 32 == 0 and P in (1, 2, 4, 8) and P >= _radius(scheme)
+
+
 def tune_single(scheme, dtype, n, probe_steps=None, cache=DEFAULT_CACHE, refresh=False, reps=2, threads=THREADS,
-                modes=(0, 1, 2)):
-    """Best (tile_w, threads, persistent, cluster) for swept_step_n on an
-    n-point problem.  Modes: 0 one launch per pass; 1 one persistent kernel;
-    2 one thread-block cluster holding every tile (tried only with at most
+                modes=(0, 1, 2), warp_tiles=True):
+    """Best (tile_w, threads, warp_tiles, persistent, cluster) for swept_step_n
+    on an n-point problem.  Tier mappings: shared-memory tiers with each of
+    `threads`, and (warp_tiles) one warp per tile with the tier rows in
+    registers.  Modes: 0 one launch per pass; 1 one persistent kernel; 2 one
+    thread-block cluster holding every tile (tried only with at most
     MAX_CLUSTER_TILES tiles)."""
     import torch
 
     table = _load(cache) if cache else {}
-    key = "single3/%s/%d/%d/%d/%s" % (_device_key(), scheme, dtype, n, probe_steps)
+    key = "single4/%s/%d/%d/%d/%s/%d" % (_device_key(), scheme, dtype, n, probe_steps, int(warp_tiles))
     if not refresh and key in table:
         return table[key]
-    u0, args, bc = _problem(scheme, dtype, n)
+    u0, args, bc = problem(scheme, dtype, n)
     h_steps = max(tile_candidates(scheme, n)) // (2 * _radius(scheme))
     steps = probe_steps or max(64, 4 * h_steps)
     best = None
     d0 = torch.from_numpy(np.ascontiguousarray(u0)).cuda()
     for W in tile_candidates(scheme, n):
-        for t in threads:
-            if t > max(32, 2 * W):
-                continue
+        mappings = [(t, 0) for t in threads if t <= max(32, 2 * W)]
+        if warp_tiles and warp_tile_ok(scheme, W):
+            mappings.append((32, 1))
+        for t, wt in mappings:
             for mode in modes:
                 if mode == 2 and n // W > MAX_CLUSTER_TILES:
                     continue
                 try:
                     sol = S.Solver(scheme, dtype, n, *args, bc=bc, tile_w=W, threads=t, persistent=int(mode == 1),
-                                   cluster=int(mode == 2))
+                                   cluster=int(mode == 2), warp_tiles=wt)
                 except S.SweptError:
                     continue  # e.g. a cluster window that does not fit in shared memory
                 u = d0.clone()
                 ms = _time(lambda: sol.step(u, steps), reps)
                 sol.close()
                 if best is None or ms < best["ms"]:
-                    best = {"tile_w": W, "threads": t, "persistent": int(mode == 1), "cluster": int(mode == 2),
-                            "ms": ms, "probe_steps": steps}
+                    best = {"tile_w": W, "threads": t, "warp_tiles": wt, "persistent": int(mode == 1),
+                            "cluster": int(mode == 2), "ms": ms, "probe_steps": steps}
     if cache:
         table = _load(cache)
         table[key] = best
         _store(cache, table)
     return best
+
+
+def solver_from_plan(scheme, dtype, n, dx, dt, param0, plan, bc=S.BC_PERIODIC):
+    """A Solver configured with a tune_single result."""
+    return S.Solver(scheme, dtype, n, dx, dt, param0, bc=bc, tile_w=plan["tile_w"], threads=plan["threads"],
+                    persistent=plan.get("persistent", 0), cluster=plan.get("cluster", 0),
+                    warp_tiles=plan.get("warp_tiles", 0))
 
 
 def tune_batch(problems, dtype, tiles=(128, 256, 512), threads=(64, 128, 256), probe_fraction=0.05,
