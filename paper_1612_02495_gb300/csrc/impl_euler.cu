@@ -21,10 +21,12 @@ cudaError_t euler_classic(const Geom& g, const void* kb, int stage, const void* 
   const unsigned grid = (unsigned)((g.N + B - 1) / B);
   const size_t smem = sizeof(T) * (3 * (B + 4) + 3 * (B + 1));
   const auto k = Launch<T, EulerOp<T>>::kc(kb);
+  // B cells per block and one more warp, so that each of the B + 1 faces
+  // has its own thread
   if (stage == 0)
-    k_classic_euler<T, 0><<<grid, B, smem, s>>>(g.N, g.bc, k, (const T*)in, (T*)out);
+    k_classic_euler<T, 0><<<grid, B + 32, smem, s>>>(g.N, g.bc, k, (const T*)in, (T*)out, B);
   else
-    k_classic_euler<T, 1><<<grid, B, smem, s>>>(g.N, g.bc, k, (const T*)in, (T*)out);
+    k_classic_euler<T, 1><<<grid, B + 32, smem, s>>>(g.N, g.bc, k, (const T*)in, (T*)out, B);
   return cudaGetLastError();
 }
 

@@ -154,7 +154,63 @@ __device__ __forceinline__ void euler_face(const T* pr, const T* pu, const T* pp
   EulerOp<T>::flux(a, b, c, d, k, F0, F1, F2);
 }
 
-template <typename T, int STAGE>
+// One side of face f for the two-threads-per-face flux phase, with one code
+// path for both sides (no divergence within a lane pair): side 0 (left)
+// reconstructs p1 + h from cells f-2, f-1, f; side 1 (right) p1 - h from
+// cells f-1, f, f+1, where h = 1/2 minmod(p1 - p0, p2 - p1).  Adding -h is
+// the same IEEE operation as subtracting h, so both sides equal
+// EulerOp::left_side / right_side bit for bit.
+template <typename T>
+__device__ __forceinline__ typename EulerOp<T>::Side euler_side(const T* pr, const T* pu, const T* pp, int f,
+                                                                int owner, int wall, int side,
+                                                                const typename EulerOp<T>::K& k) {
+  const auto p0 = euler_read_prim<T>(pr, pu, pp, owner, f - 2 + side - owner, wall);
+  const auto p1 = euler_read_prim<T>(pr, pu, pp, owner, f - 1 + side - owner, wall);
+  const auto p2 = euler_read_prim<T>(pr, pu, pp, owner, f + side - owner, wall);
+  typename EulerOp<T>::Side X;
+  const T hr = mul_rn(T(0.5), minmod(sub_rn(p1.r, p0.r), sub_rn(p2.r, p1.r)));
+  const T hu = mul_rn(T(0.5), minmod(sub_rn(p1.u, p0.u), sub_rn(p2.u, p1.u)));
+  const T hp = mul_rn(T(0.5), minmod(sub_rn(p1.p, p0.p), sub_rn(p2.p, p1.p)));
+  X.r = add_rn(p1.r, side ? -hr : hr);
+  X.u = add_rn(p1.u, side ? -hu : hu);
+  X.p = add_rn(p1.p, side ? -hp : hp);
+  EulerOp<T>::finish_side(X, k);
+  return X;
+}
+
+// the flux of face f by a lane pair (lanes 2t, 2t+1 of `mask`): each lane
+// builds its side, the pair swaps sides by shuffle, the left lane forms
+// F0, F1 and the right lane F2; stored only when `store`
+template <typename T>
+__device__ __forceinline__ void euler_face_pair(const T* pr, const T* pu, const T* pp, int f, int owner, int wall,
+                                                int side, bool store, unsigned mask,
+                                                const typename EulerOp<T>::K& k, T* F0, T* F1, T* F2) {
+  using Side = typename EulerOp<T>::Side;
+  const Side X = euler_side<T>(pr, pu, pp, f, owner, wall, side, k);
+  Side Y;
+  Y.r = __shfl_xor_sync(mask, X.r, 1);
+  Y.u = __shfl_xor_sync(mask, X.u, 1);
+  Y.p = __shfl_xor_sync(mask, X.p, 1);
+  Y.m = __shfl_xor_sync(mask, X.m, 1);
+  Y.E = __shfl_xor_sync(mask, X.E, 1);
+  Y.sp = __shfl_xor_sync(mask, X.sp, 1);
+  const Side L = side ? Y : X;
+  const Side R = side ? X : Y;
+  const T s = EulerOp<T>::smax(L, R);
+  if (side == 0) {
+    const T a0 = EulerOp<T>::flux0(L, R, s);
+    const T a1 = EulerOp<T>::flux1(L, R, s);
+    if (store) {
+      *F0 = a0;
+      *F1 = a1;
+    }
+  } else {
+    const T a2 = EulerOp<T>::flux2(L, R, s);
+    if (store) *F2 = a2;
+  }
+}
+
+template <typename T, int STAGE, bool PAIR = false>
 __device__ __forceinline__ void euler_level(T* sm, int M, int out_row, int lo, int hi, int wall,
                                             const typename EulerOp<T>::K& k) {
   const T* in0 = sm + ((out_row ^ 1) * 3 + 0) * M;
@@ -177,13 +233,38 @@ __device__ __forceinline__ void euler_level(T* sm, int M, int out_row, int lo, i
     pp[q] = w.p;
   }
   __syncthreads();
-  for (int f = lo + (int)threadIdx.x; f <= hi; f += (int)blockDim.x) {
-    if (f == wall) {
-      euler_face<T>(pr, pu, pp, f, f, wall, k, F0[f], F1[f], F2[f]);
-      euler_face<T>(pr, pu, pp, f, f - 1, wall, k, Fw[0], Fw[1], Fw[2]);
-    } else {
-      const int owner = (wall == NO_WALL || f > wall) ? f : f - 1;
-      euler_face<T>(pr, pu, pp, f, owner, wall, k, F0[f], F1[f], F2[f]);
+  // Work items of the flux phase: faces lo..hi (item f - lo), and for a wall
+  // face inside the range also its flux seen from the left cell (item nf),
+  // handed to its own thread so the wall costs no thread a second flux.
+  const int nf = hi - lo + 1;
+  const int nitems = nf + ((wall != NO_WALL && wall >= lo && wall <= hi) ? 1 : 0);
+  if (!PAIR) {
+    for (int i = (int)threadIdx.x; i < nitems; i += (int)blockDim.x) {
+      if (i < nf) {
+        const int f = lo + i;
+        const int owner = (wall == NO_WALL || f >= wall) ? f : f - 1;
+        euler_face<T>(pr, pu, pp, f, owner, wall, k, F0[f], F1[f], F2[f]);
+      } else {
+        euler_face<T>(pr, pu, pp, wall, wall - 1, wall, k, Fw[0], Fw[1], Fw[2]);
+      }
+    }
+  } else {
+    // two threads per item; the trip count is the same for all lanes of a
+    // warp (a warp leaves once its first pair is past the last item), so
+    // every lane of a working warp reaches the shuffles (pairs past the end
+    // recompute the last item and store nothing)
+    const int half = (int)blockDim.x >> 1;
+    const int side = (int)threadIdx.x & 1;
+    const int t = (int)threadIdx.x >> 1;
+    const int t_warp = (int)(threadIdx.x & ~31u) >> 1;  // first pair of this warp
+    for (int base = 0; base + t_warp < nitems; base += half) {
+      const bool act = base + t < nitems;
+      const int i = act ? base + t : nitems - 1;
+      const bool second = i == nf;  // the wall face seen from its left cell
+      const int f = second ? wall : lo + i;
+      const int owner = second ? wall - 1 : ((wall == NO_WALL || f >= wall) ? f : f - 1);
+      euler_face_pair<T>(pr, pu, pp, f, owner, wall, side, act, 0xffffffffu, k, second ? Fw : F0 + f,
+                         second ? Fw + 1 : F1 + f, second ? Fw + 2 : F2 + f);
     }
   }
   __syncthreads();
@@ -211,14 +292,22 @@ struct LevelImpl {
       scalar_level_any<T, Op, 1>(sm, M, out_row, lo, hi, wall, chunk, k);
   }
 };
+// Euler: chunk 2 = two threads per face in the flux phase
 template <typename T>
 struct LevelImpl<T, EulerOp<T>> {
   __device__ __forceinline__ static void run(T* sm, int M, int stage, int out_row, int lo, int hi, int wall,
-                                             int /*chunk*/, const typename EulerOp<T>::K& k) {
-    if (stage == 0)
-      euler_level<T, 0>(sm, M, out_row, lo, hi, wall, k);
-    else
-      euler_level<T, 1>(sm, M, out_row, lo, hi, wall, k);
+                                             int chunk, const typename EulerOp<T>::K& k) {
+    if (chunk == 2) {
+      if (stage == 0)
+        euler_level<T, 0, true>(sm, M, out_row, lo, hi, wall, k);
+      else
+        euler_level<T, 1, true>(sm, M, out_row, lo, hi, wall, k);
+    } else {
+      if (stage == 0)
+        euler_level<T, 0>(sm, M, out_row, lo, hi, wall, k);
+      else
+        euler_level<T, 1>(sm, M, out_row, lo, hi, wall, k);
+    }
   }
 };
 
@@ -816,14 +905,14 @@ __global__ void __launch_bounds__(256) k_classic(int64_t N, int bc, typename Op:
   out[i] = Op::template point<STAGE>(v, p2, k);
 }
 
-// Euler classic stage: a block of blockDim.x cells stages conserved values and
-// primitives of its cells plus 2 halo cells per side in shared memory, computes
-// its blockDim.x + 1 face fluxes once, then updates its cells.
+// Euler classic stage: a block of B cells stages the primitives of its cells
+// plus 2 halo cells per side in shared memory, computes its B + 1 face fluxes
+// once (one thread each: the block has B + 32 threads), then updates its cells.
 template <typename T, int STAGE>
-__global__ void __launch_bounds__(256) k_classic_euler(int64_t N, int bc, typename EulerOp<T>::K k,
-                                                       const T* __restrict__ in, T* out) {
+__global__ void __launch_bounds__(288) k_classic_euler(int64_t N, int bc, typename EulerOp<T>::K k,
+                                                       const T* __restrict__ in, T* out, int B) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int B = blockDim.x;
+  // B cells per block; blockDim = B + 32, so each of the B + 1 faces has its own thread
   const int Wn = B + 4;
   T* pr = reinterpret_cast<T*>(smraw);
   T* pu = pr + Wn;
@@ -832,7 +921,7 @@ __global__ void __launch_bounds__(256) k_classic_euler(int64_t N, int bc, typena
   T* F1 = F0 + (B + 1);
   T* F2 = F1 + (B + 1);
   const int64_t i0 = (int64_t)blockIdx.x * B;
-  for (int t = threadIdx.x; t < Wn; t += B) {
+  for (int t = threadIdx.x; t < Wn; t += (int)blockDim.x) {
     const int64_t x = i0 - 2 + t;
     if (x - 2 >= N) continue;  // beyond the last block's last face stencil
     bool flip;
@@ -844,7 +933,7 @@ __global__ void __launch_bounds__(256) k_classic_euler(int64_t N, int bc, typena
     pp[t] = w.p;
   }
   __syncthreads();
-  for (int f = threadIdx.x; f <= B; f += B) {
+  for (int f = threadIdx.x; f <= B; f += (int)blockDim.x) {
     if (i0 + f > N) continue;
     typename EulerOp<T>::Prim a{pr[f], pu[f], pp[f]}, b{pr[f + 1], pu[f + 1], pp[f + 1]},
         c{pr[f + 2], pu[f + 2], pp[f + 2]}, d{pr[f + 3], pu[f + 3], pp[f + 3]};
@@ -853,7 +942,7 @@ __global__ void __launch_bounds__(256) k_classic_euler(int64_t N, int bc, typena
   __syncthreads();
   const int t = threadIdx.x;
   const int64_t i = i0 + t;
-  if (i >= N) return;
+  if (t >= B || i >= N) return;
 #pragma unroll
   for (int cc = 0; cc < 3; ++cc) {
     const T* F = cc == 0 ? F0 : (cc == 1 ? F1 : F2);

@@ -113,38 +113,56 @@ struct EulerOp {
     w.p = mul_rn(k.gm1, fma_rn(-mul_rn(T(0.5), m), w.u, e));
     return w;
   }
+  // One side of a face: the MUSCL-minmod reconstructed state with its
+  // momentum, energy and wave-speed bound.  Left side from cells a, b, c
+  // (value at the right end of b), right side from b, c, d (left end of c).
+  struct Side {
+    T r, u, p, m, E, sp;
+  };
+  __device__ __forceinline__ static void finish_side(Side& X, const K& k) {
+    X.m = mul_rn(X.r, X.u);
+    X.E = fma_rn(mul_rn(T(0.5), X.m), X.u, mul_rn(X.p, k.igm1));
+    const T c = sqrt_rn(div_rn(mul_rn(k.gamma, X.p), X.r));
+    X.sp = add_rn(fabs(X.u), c);
+  }
+  __device__ __forceinline__ static Side left_side(const Prim& a, const Prim& b, const Prim& c, const K& k) {
+    Side L;
+    L.r = add_rn(b.r, mul_rn(T(0.5), minmod(sub_rn(b.r, a.r), sub_rn(c.r, b.r))));
+    L.u = add_rn(b.u, mul_rn(T(0.5), minmod(sub_rn(b.u, a.u), sub_rn(c.u, b.u))));
+    L.p = add_rn(b.p, mul_rn(T(0.5), minmod(sub_rn(b.p, a.p), sub_rn(c.p, b.p))));
+    finish_side(L, k);
+    return L;
+  }
+  __device__ __forceinline__ static Side right_side(const Prim& b, const Prim& c, const Prim& d, const K& k) {
+    Side R;
+    R.r = sub_rn(c.r, mul_rn(T(0.5), minmod(sub_rn(c.r, b.r), sub_rn(d.r, c.r))));
+    R.u = sub_rn(c.u, mul_rn(T(0.5), minmod(sub_rn(c.u, b.u), sub_rn(d.u, c.u))));
+    R.p = sub_rn(c.p, mul_rn(T(0.5), minmod(sub_rn(c.p, b.p), sub_rn(d.p, c.p))));
+    finish_side(R, k);
+    return R;
+  }
+  // Rusanov flux from the two sides: 1/2 (F(L) + F(R)) - 1/2 s (U_R - U_L),
+  // s = the larger of |u| + c over the two sides
+  __device__ __forceinline__ static T smax(const Side& L, const Side& R) { return L.sp >= R.sp ? L.sp : R.sp; }
+  __device__ __forceinline__ static T flux0(const Side& L, const Side& R, T s) {
+    return mul_rn(T(0.5), fma_rn(-s, sub_rn(R.r, L.r), add_rn(L.m, R.m)));
+  }
+  __device__ __forceinline__ static T flux1(const Side& L, const Side& R, T s) {
+    return mul_rn(T(0.5), fma_rn(-s, sub_rn(R.m, L.m), add_rn(fma_rn(L.m, L.u, L.p), fma_rn(R.m, R.u, R.p))));
+  }
+  __device__ __forceinline__ static T flux2(const Side& L, const Side& R, T s) {
+    return mul_rn(T(0.5),
+                  fma_rn(-s, sub_rn(R.E, L.E), add_rn(mul_rn(L.u, add_rn(L.E, L.p)), mul_rn(R.u, add_rn(R.E, R.p)))));
+  }
   // Rusanov flux through the face between cells b and c, from cells a, b, c, d
   __device__ __forceinline__ static void flux(const Prim& a, const Prim& b, const Prim& c, const Prim& d, const K& k,
                                               T& F0, T& F1, T& F2) {
-    Prim L, Rt;
-    {
-      const T dl = sub_rn(b.r, a.r), dc = sub_rn(c.r, b.r), dr = sub_rn(d.r, c.r);
-      L.r = add_rn(b.r, mul_rn(T(0.5), minmod(dl, dc)));
-      Rt.r = sub_rn(c.r, mul_rn(T(0.5), minmod(dc, dr)));
-    }
-    {
-      const T dl = sub_rn(b.u, a.u), dc = sub_rn(c.u, b.u), dr = sub_rn(d.u, c.u);
-      L.u = add_rn(b.u, mul_rn(T(0.5), minmod(dl, dc)));
-      Rt.u = sub_rn(c.u, mul_rn(T(0.5), minmod(dc, dr)));
-    }
-    {
-      const T dl = sub_rn(b.p, a.p), dc = sub_rn(c.p, b.p), dr = sub_rn(d.p, c.p);
-      L.p = add_rn(b.p, mul_rn(T(0.5), minmod(dl, dc)));
-      Rt.p = sub_rn(c.p, mul_rn(T(0.5), minmod(dc, dr)));
-    }
-    const T mL = mul_rn(L.r, L.u);
-    const T mR = mul_rn(Rt.r, Rt.u);
-    const T EL = fma_rn(mul_rn(T(0.5), mL), L.u, mul_rn(L.p, k.igm1));
-    const T ER = fma_rn(mul_rn(T(0.5), mR), Rt.u, mul_rn(Rt.p, k.igm1));
-    const T cL = sqrt_rn(div_rn(mul_rn(k.gamma, L.p), L.r));
-    const T cR = sqrt_rn(div_rn(mul_rn(k.gamma, Rt.p), Rt.r));
-    const T sL = add_rn(fabs(L.u), cL);
-    const T sR = add_rn(fabs(Rt.u), cR);
-    const T s = sL >= sR ? sL : sR;
-    F0 = mul_rn(T(0.5), fma_rn(-s, sub_rn(Rt.r, L.r), add_rn(mL, mR)));
-    F1 = mul_rn(T(0.5), fma_rn(-s, sub_rn(mR, mL), add_rn(fma_rn(mL, L.u, L.p), fma_rn(mR, Rt.u, Rt.p))));
-    F2 = mul_rn(T(0.5),
-                fma_rn(-s, sub_rn(ER, EL), add_rn(mul_rn(L.u, add_rn(EL, L.p)), mul_rn(Rt.u, add_rn(ER, Rt.p)))));
+    const Side L = left_side(a, b, c, k);
+    const Side R = right_side(b, c, d, k);
+    const T s = smax(L, R);
+    F0 = flux0(L, R, s);
+    F1 = flux1(L, R, s);
+    F2 = flux2(L, R, s);
   }
   template <int STAGE>
   __device__ __forceinline__ static T update(T fp, T fm, T in_self, T prev2, const K& k) {

@@ -398,3 +398,50 @@ def test_warp_tiles_parity(S, scheme, dtype, n, W, nsteps, bc, mode):
     assert np.array_equal(got, ref)
     sol.close()
     smem.close()
+
+
+EULER_PAIR_CASES = [
+    # dtype, n, W, threads, nsteps, bc, mode (0 per pass, 1 persistent, 2 cluster)
+    (np.float64, 1024, 64, 64, 300, 1, 0),
+    (np.float32, 1024, 64, 128, 300, 0, 0),
+    (np.float64, 3 * 32, 32, 32, 77, 1, 0),    # the wall face inside a 32-thread block
+    (np.float64, 2 * 8, 8, 32, 13, 1, 0),      # minimum tile and grid
+    (np.float64, 1 << 16, 256, 128, 300, 1, 0),
+    (np.float64, 1 << 16, 256, 256, 301, 1, 1),
+    (np.float32, 8 * 128, 128, 64, 99, 1, 2),
+]
+
+
+@pytest.mark.parametrize("dtype,n,W,threads,nsteps,bc,mode", EULER_PAIR_CASES)
+def test_euler_pair_flux_parity(S, dtype, n, W, threads, nsteps, bc, mode):
+    """Euler with two threads per face in the flux phase (chunk 2): equal to
+    one thread per face, classic and the oracle bit for bit."""
+    import torch
+
+    pr = inputs.euler_problem(n=n, dtype=dtype)
+    U0 = pr["U0"]
+    if bc == 0:
+        x = (np.arange(n) + 0.5) / n
+        rho = 1 + 0.2 * np.sin(2 * np.pi * x)
+        u = 0.3 + 0.1 * np.cos(2 * np.pi * x)
+        p = 1 + 0.1 * np.sin(4 * np.pi * x)
+        U0 = np.stack([rho, rho * u, p / 0.4 + 0.5 * rho * u * u]).astype(dtype)
+    code = S.F64 if dtype == np.float64 else S.F32
+    args = (pr["dx"], pr["dt"], pr["gamma"])
+    pair = S.Solver(S.EULER, code, n, *args, bc=bc, tile_w=W, threads=threads, chunk=2, persistent=int(mode == 1),
+                    cluster=int(mode == 2))
+    one = S.Solver(S.EULER, code, n, *args, bc=bc, tile_w=W, threads=threads)
+    a = torch.from_numpy(np.ascontiguousarray(U0)).cuda()
+    b, c = a.clone(), a.clone()
+    pair.step(a, nsteps)
+    one.step(b, nsteps)
+    one.classic(c, nsteps)
+    torch.cuda.synchronize()
+    pair.sync_status()
+    got = a.cpu().numpy()
+    assert np.array_equal(got, b.cpu().numpy())
+    assert np.array_equal(got, c.cpu().numpy())
+    ref = oracle.euler(U0, pr["dx"], pr["dt"], pr["gamma"], nsteps, bc=bc, threads=THREADS)
+    assert np.array_equal(got, ref)
+    pair.close()
+    one.close()
