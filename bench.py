@@ -42,7 +42,7 @@ FP64_INSTR_PEAK = 152 * 2 * 2.07e9
 FP64_KS_MIX_CEILING = 0.535e12
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_swept_diamond<double, KsOp> launch at
 # N = 2^20, tile 1024 (ncu, profiles/k_swept_diamond_ks_f64_n1048576.md); None once the kernel changes
-DIAMOND_TRAFFIC_BYTES = 16824832
+DIAMOND_TRAFFIC_BYTES = None
 # same for one k_swept_persist<double, KsOp> launch (a whole solve); None until captured
 PERSIST_TRAFFIC_BYTES = None
 

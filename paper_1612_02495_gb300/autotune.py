@@ -20,7 +20,7 @@ from . import inputs
 from . import swept as S
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_1612_02495_gb300", "tune.json")
-THREADS = (32, 64, 128, 256)
+THREADS = (32, 64, 128, 256, 512)
 MAX_CLUSTER_TILES = 16  # the largest (non-portable) thread-block cluster
 
 
