@@ -32,6 +32,7 @@ UNIT = "cell-updates/s"
 WORKLOAD = "Kuramoto-Sivashinsky N=2^20 FP64 periodic, 50,000 midpoint-RK2 steps (dt=0.005, dx=pi/4)"
 FP64_FLOPS_PER_SUBSTEP = 18  # 7 fma (2 flops) + 2 add + 2 mul per point per sub-timestep
 FP64_INSTR_PER_SUBSTEP = 11
+CLASSIC_BYTES_PER_UPDATE = 40
 # FP64 roof of GB300: 152 SMs x 2 DFMA per clock x 2 flops x 2.07 GHz (nominal 1.25 TFLOP/s);
 # the issue-rate probe measured 0.60e12 DFMA/s.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -43,8 +44,11 @@ FP64_KS_MIX_CEILING = 0.535e12
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_swept_diamond<double, KsOp> launch at
 # N = 2^20, tile 1024 (ncu, profiles/k_swept_diamond_ks_f64_n1048576.md); None once the kernel changes
 DIAMOND_TRAFFIC_BYTES = None
-# same for one k_swept_persist<double, KsOp> launch (a whole solve); None until captured
-PERSIST_TRAFFIC_BYTES = None
+# same for one k_swept_persist<double, KsOp> launch of the bench's tuned plan (tile 1024, 256 threads,
+# a whole 50,000-step solve): 10.36 MB read + 28.67 MB written (profiles/k_swept_persist_ks_f64_n1048576.md);
+# None once the kernel or the plan changes
+PERSIST_TRAFFIC_BYTES = 39030000
+PERSIST_TRAFFIC_PLAN = (1024, 256)
 
 
 def peaks():
@@ -256,18 +260,19 @@ def measure_batch(S, inputs, autotune, torch, stream, barrier, ws, with_f64):
     return out
 
 
-# swept (tuned plan) vs classic across the paper's sizes; (label, scheme, dtype, n, steps, tuner probe steps)
+# swept (tuned plan) vs classic across the paper's sizes:
+# (label, scheme, dtype, n, steps, tuner probe steps, timed repeats)
 SIZE_CASES = [
-    ("heat N=2^10 FP64 periodic, 10,000 steps", "heat", "f64", 1 << 10, 10000, 2000),
-    ("heat N=2^10 FP32 periodic, 10,000 steps", "heat", "f32", 1 << 10, 10000, 2000),
-    ("KS N=2^14 FP64, 5,000 steps", "ks", "f64", 1 << 14, 5000, 1000),
-    ("KS N=2^14 FP32, 5,000 steps", "ks", "f32", 1 << 14, 5000, 1000),
-    ("KS N=2^16 FP64, 5,000 steps", "ks", "f64", 1 << 16, 5000, 1000),
-    ("KS N=2^16 FP32, 5,000 steps", "ks", "f32", 1 << 16, 5000, 1000),
-    ("KS N=2^18 FP64, 2,000 steps", "ks", "f64", 1 << 18, 2000, 1000),
-    ("KS N=2^18 FP32, 2,000 steps", "ks", "f32", 1 << 18, 2000, 1000),
-    ("Euler Sod N=2^16 FP64 reflective, 300 steps", "euler", "f64", 1 << 16, 300, 200),
-    ("Euler Sod N=2^20 FP64 reflective, 100 steps", "euler", "f64", 1 << 20, 100, 100),
+    ("heat N=2^10 FP64 periodic, 10,000 steps", "heat", "f64", 1 << 10, 10000, 2000, 3),
+    ("heat N=2^10 FP32 periodic, 10,000 steps", "heat", "f32", 1 << 10, 10000, 2000, 3),
+    ("KS N=2^14 FP64, 5,000 steps", "ks", "f64", 1 << 14, 5000, 1000, 3),
+    ("KS N=2^14 FP32, 5,000 steps", "ks", "f32", 1 << 14, 5000, 1000, 3),
+    ("KS N=2^16 FP64, 5,000 steps", "ks", "f64", 1 << 16, 5000, 1000, 3),
+    ("KS N=2^16 FP32, 5,000 steps", "ks", "f32", 1 << 16, 5000, 1000, 3),
+    ("KS N=2^18 FP64, 2,000 steps", "ks", "f64", 1 << 18, 2000, 1000, 3),
+    ("KS N=2^18 FP32, 2,000 steps", "ks", "f32", 1 << 18, 2000, 1000, 3),
+    ("Euler Sod N=2^16 FP64 reflective, to t=0.2 (81,920 steps)", "euler", "f64", 1 << 16, 81920, 200, 1),
+    ("Euler Sod N=2^20 FP64 reflective, 100 steps", "euler", "f64", 1 << 20, 100, 100, 3),
 ]
 
 
@@ -277,7 +282,7 @@ def measure_sizes(S, autotune, torch, stream, barrier, ws, flush):
     timed solve, best of three)."""
     codes = {"heat": S.HEAT, "ks": S.KS, "euler": S.EULER}
     out = []
-    for label, scheme, dt, n, nsteps, probe in SIZE_CASES:
+    for label, scheme, dt, n, nsteps, probe, reps in SIZE_CASES:
         sc, code = codes[scheme], (S.F64 if dt == "f64" else S.F32)
         u0, args, bc = autotune.problem(sc, code, n)
         plan = autotune.tune_single(sc, code, n, probe_steps=probe)
@@ -288,7 +293,7 @@ def measure_sizes(S, autotune, torch, stream, barrier, ws, flush):
         for name, fn in (("swept", sol.step), ("classic", sol.classic)):
             fn(u, nsteps)
             best = None
-            for _ in range(3):
+            for _ in range(reps):
                 u.copy_(d0)
                 flush.zero_()
                 ev = _event_time(torch, stream, lambda: fn(u, nsteps))
@@ -442,6 +447,8 @@ def main():
                     "pipe_frac": FP64_INSTR_PER_SUBSTEP * units / (ms * 1e-3) / FP64_INSTR_PEAK,
                     "frac_of_measured_mix_ceiling": FP64_INSTR_PER_SUBSTEP * units / (ms * 1e-3) / FP64_KS_MIX_CEILING,
                     "kernel_ms_avg": ms, "kernel_share": 1.0}
+        if (plan["tile_w"], plan["threads"]) != PERSIST_TRAFFIC_PLAN or plan.get("warp_tiles"):
+            roofline["traffic"] = None  # the ncu figure is for the tile-1024, 256-thread plan
         roofline["frac"] = roofline["achieved"] / FP64_PEAK_TFLOPS
         launches_per_step = 2
     else:
@@ -497,14 +504,26 @@ def main():
     out["config"]["autotuned"] = {k: tuned.get(k, 0) for k in ("tile_w", "threads", "warp_tiles", "persistent",
                                                                 "cluster")}
     if ms_classic:
-        out["classic"] = {"value": ws * N * NSTEPS / (ms_classic * 1e-3), "ms_per_step": ms_classic}
+        # classic moves the state through HBM/L2 every sub-timestep: stage 0 reads u and writes P,
+        # stage 1 reads P and u and writes u: 5 values = 40 B per cell-update in FP64
+        gbs = CLASSIC_BYTES_PER_UPDATE * N * NSTEPS / (ms_classic * 1e-3) / 1e9
+        hbm = peaks().get("hbm_gbs")
+        out["classic"] = {"value": ws * N * NSTEPS / (ms_classic * 1e-3), "ms_per_step": ms_classic,
+                          "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                       "frac": (gbs / hbm) if hbm else None,
+                                       "algorithmic_bytes_per_cell_update": CLASSIC_BYTES_PER_UPDATE,
+                                       "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                                       "note": "FP64 classic is bound by the FP64 pipe, not HBM"}}
         out["speedup_vs_classic"] = ms_classic / ms
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         r, st, secs = cpu_oracle_rate(N, 10.0, threads)
+        r1, st1, secs1 = cpu_oracle_rate(N, 4.0, 1)
         out["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
                                "sample": "oracle on the full N=2^20 grid for %d steps (%.1f s, OpenMP %d threads)"
-                                         % (st, secs, threads)}
+                                         % (st, secs, threads),
+                               "one_thread": {"value": r1, "unit": UNIT, "cores": 1,
+                                              "sample": "same grid, %d steps (%.1f s, 1 thread)" % (st1, secs1)}}
     if rank == 0:
         print(json.dumps(out))
     sol.close()
