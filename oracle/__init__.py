@@ -11,6 +11,7 @@ Schemes (Magee & Niemeyer, arXiv:1612.02495):
   heat   FTCS, Eq. HeatDisc                                   (periodic or insulated)
   ks     Eq. KSDisc (u_i term read as -2 u_i) + midpoint RK2, Appendix (periodic)
   euler  MUSCL-minmod + Rusanov + SSP-RK2 (not in the paper)  (periodic or reflective)
+  heat2d FTCS 5-point, the 2D extension of Eq. HeatDisc       (periodic or insulated)
 Adjoints (not in the paper): exact discrete reverse mode of the FP64 forward.
 
 Boundary codes used here: BC_PERIODIC = 0, BC_MIRROR = 1.
@@ -43,6 +44,7 @@ def lib():
             getattr(L, "oracle_ks_run_" + sfx).argtypes = [_P, _I64, _D, _D, _D, _I64, _INT]
             getattr(L, "oracle_euler_run_" + sfx).argtypes = [_P, _I64, _D, _D, _D, _INT, _I64, _INT]
             getattr(L, "oracle_euler_stage_" + sfx).argtypes = [_P, _P, _I64, _D, _D, _D, _INT]
+            getattr(L, "oracle_heat2d_run_" + sfx).argtypes = [_P, _I64, _I64, _D, _D, _D, _INT, _I64, _INT]
         L.oracle_ks_adjoint_f64.argtypes = [_P, _I64, _D, _D, _D, _I64, _P, _P, _P, _I64, _P]
         L.oracle_heat_adjoint_f64.argtypes = [_P, _I64, _D, _D, _D, _INT, _I64, _P, _P, _P, _P]
         L.oracle_max_threads.restype = _INT
@@ -78,6 +80,18 @@ def heat(u0, dx, dt, alpha, nsteps, bc=BC_PERIODIC, threads=1):
     u = np.array(u0, copy=True, order="C")
     _check(getattr(lib(), "oracle_heat_run_" + _sfx(u.dtype))(_ptr(u), u.size, dx, dt, alpha, bc, nsteps, threads),
            "heat")
+    return u
+
+
+def heat2d(u0, dx, dt, alpha, nsteps, bc=BC_PERIODIC, threads=1):
+    """2D FTCS heat equation on a square-celled grid; u0 has shape (ny, nx) (row-major,
+    x fastest).  Returns u0 advanced `nsteps` steps (new array, dtype kept)."""
+    u = np.array(u0, copy=True, order="C")
+    if u.ndim != 2:
+        raise ValueError("heat2d state must have shape (ny, nx)")
+    ny, nx = u.shape
+    _check(getattr(lib(), "oracle_heat2d_run_" + _sfx(u.dtype))(_ptr(u), nx, ny, dx, dt, alpha, bc, nsteps, threads),
+           "heat2d")
     return u
 
 

@@ -14,20 +14,21 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "swept_oracle.c")
+SRC2D = os.path.join(HERE, "heat2d.c")
 INC = os.path.join(HERE, "scheme_body.inc")
 LIB = os.path.join(HERE, "liboracle.so")
 
 
 def _compile(extra):
     cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-Wall", "-o", LIB + ".tmp", SRC] + extra + ["-lm"]
+           "-Wall", "-o", LIB + ".tmp", SRC, SRC2D] + extra + ["-lm"]
     return subprocess.run(cmd, capture_output=True, text=True)
 
 
 def build(force=False):
     """Compile liboracle.so if it is missing or older than its sources; return its path."""
     if not force and os.path.exists(LIB):
-        newest = max(os.path.getmtime(SRC), os.path.getmtime(INC))
+        newest = max(os.path.getmtime(SRC), os.path.getmtime(SRC2D), os.path.getmtime(INC))
         if os.path.getmtime(LIB) >= newest:
             return LIB
     r = _compile(["-fopenmp"])

@@ -42,6 +42,30 @@ def heat_problem(n=1024, r=0.25, alpha=1.0, modes=8, seed=0, dtype=np.float64):
     return dict(u0=u0.astype(dtype), dx=dx, dt=dt, alpha=alpha, amps=amps, x=x, r=r)
 
 
+def heat2d_problem(nx=1024, ny=None, r=0.2, alpha=1.0, modes=4, seed=5, dtype=np.float64, noise=1e-3):
+    """Periodic 2D heat problem on square cells, dx = 2 pi / nx (so the grid covers
+    [0, 2 pi) x [0, 2 pi ny / nx)); u0 of shape (ny, nx) (x fastest) is
+    sum_{k,l=1..modes} a_kl sin(2 pi k x / Lx) sin(2 pi l y / Ly), a_kl ~ U(-1, 1),
+    plus noise * U(-1, 1) per point.  Fo = r (stable for r <= 1/4).  Returns a
+    dict with u0, dx, dt, alpha, amps (modes x modes), r."""
+    ny = nx if ny is None else ny
+    dx = 2.0 * math.pi / nx
+    dt = r * (dx * dx) / alpha
+    g = rng(seed)
+    amps = g.uniform(-1.0, 1.0, size=(modes, modes))
+    x = np.arange(nx, dtype=np.float64) * dx
+    y = np.arange(ny, dtype=np.float64) * dx
+    Lx, Ly = nx * dx, ny * dx
+    u0 = np.zeros((ny, nx), dtype=np.float64)
+    for k in range(1, modes + 1):
+        sx = np.sin(2.0 * math.pi * k * x / Lx)
+        for l in range(1, modes + 1):
+            u0 += amps[k - 1, l - 1] * np.outer(np.sin(2.0 * math.pi * l * y / Ly), sx)
+    if noise:
+        u0 += noise * g.uniform(-1.0, 1.0, size=(ny, nx))
+    return dict(u0=u0.astype(dtype), dx=dx, dt=dt, alpha=alpha, amps=amps, r=r)
+
+
 def ks_length(n):
     """Domain length for N points: 32 pi N / 128 (dx = pi / 4)."""
     return 32.0 * math.pi * n / 128.0

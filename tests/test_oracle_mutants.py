@@ -34,6 +34,11 @@ MUTANTS = {
     "euler_energy_flux": ("L[1] * (EL + L[2]) + R[1] * (ER + R[2])", "L[1] * (EL) + R[1] * (ER + R[2])"),
     "euler_rk2_average": ("U[c * n + i] = (REAL)0.5 * (U[c * n + i] + t);", "U[c * n + i] = t;"),
     "euler_wall_momentum": ("if (flip) *flip = 1;", "if (flip) *flip = 0;"),
+    "heat2d_centre_weight": ("const REAL c1 = (REAL)(1.0 - 4.0 * fo_d);", "const REAL c1 = (REAL)(1.0 - 2.0 * fo_d);"),
+    "heat2d_y_neighbour": ("jn = h2_index(j + 1, ny, bc);", "jn = h2_index(j + 2, ny, bc);"),
+    "heat2d_dropped_north": ("const REAL sy = u[js * nx + i] + u[jn * nx + i];",
+                             "const REAL sy = u[js * nx + i] + u[js * nx + i];"),
+    "heat2d_mirror_index": ("return j < 0 ? -1 - j : 2 * n - 1 - j;", "return j < 0 ? -j : 2 * n - 1 - j;"),
     "adjoint_advection_sign": ("const double nl = (ca2 * w[j]) * dl;", "const double nl = (ca2 * w[j]) * (-dl);"),
     "adjoint_wrong_state": ("cur[j] = fma(k.mdth, ks_gT(mu, tu, j, n, ca2, k.c2, k.c4), lam[j] + mu[j]);",
                             "cur[j] = fma(k.mdth, ks_gT(mu, tp, j, n, ca2, k.c2, k.c4), lam[j] + mu[j]);"),
@@ -46,7 +51,7 @@ def test_pins_catch_mutant(name, tmp_path):
     shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle",
                     ignore=shutil.ignore_patterns("*.so", "*.tmp", "__pycache__"))
     planted = 0
-    for fn in ("swept_oracle.c", "scheme_body.inc"):
+    for fn in ("swept_oracle.c", "scheme_body.inc", "heat2d.c"):
         p = tmp_path / "oracle" / fn
         src = p.read_text()
         if before in src:

@@ -297,3 +297,108 @@ def test_heat_adjoint_closed_form(bc):
     Lp = gT @ oracle.heat(u0, dx, dt, alpha + h, steps, bc=bc)
     Lm = gT @ oracle.heat(u0, dx, dt, alpha - h, steps, bc=bc)
     assert abs((Lp - Lm) / (2 * h) - ga) <= 1e-7 * abs(ga) + 1e-10
+
+
+# ---------------------------------------------------------------------------
+# 2D heat (FTCS 5-point; the 2D extension of Eq. HeatDisc)
+# ---------------------------------------------------------------------------
+
+def heat2d_exact_periodic(prob, nsteps):
+    """Exact discrete solution on product sine modes, in long double:
+    sin(2 pi k i / nx) sin(2 pi l j / ny) is an eigenvector of one step with factor
+    g_kl = 1 - 4 Fo sin^2(pi k / nx) - 4 Fo sin^2(pi l / ny)."""
+    ny, nx = prob["u0"].shape
+    ld = np.longdouble
+    fo = ld(prob["alpha"]) * ld(prob["dt"]) / (ld(prob["dx"]) * ld(prob["dx"]))
+    pi = ld(np.pi)
+    i = np.arange(nx, dtype=ld)
+    j = np.arange(ny, dtype=ld)
+    out = np.zeros((ny, nx), dtype=ld)
+    m = prob["amps"].shape[0]
+    for k in range(1, m + 1):
+        for l in range(1, m + 1):
+            g = ld(1) - ld(4) * fo * np.sin(pi * k / nx) ** 2 - ld(4) * fo * np.sin(pi * l / ny) ** 2
+            out += ld(prob["amps"][k - 1, l - 1]) * g ** nsteps * np.outer(np.sin(ld(2) * pi * l * j / ny),
+                                                                         np.sin(ld(2) * pi * k * i / nx))
+    return out
+
+
+def test_heat2d_exact_discrete_solution_periodic():
+    """2D heat on a 128 x 96 grid (non-square, so a transposed index fails), 2,000 steps,
+    against the product-mode closed form (<= 1e-12).  The grid is large enough that the
+    slowest mode keeps 1 % of its amplitude, so the bound is not inflated by decay."""
+    p = inputs.heat2d_problem(nx=128, ny=96, noise=0.0)
+    u = oracle.heat2d(p["u0"], p["dx"], p["dt"], p["alpha"], 2000)
+    assert relerr(u, heat2d_exact_periodic(p, 2000)) <= 1e-12
+
+
+def test_heat2d_insulated_eigenvector():
+    """Insulated (mirror) walls: cos(pi k (i + 1/2) / nx) cos(pi l (j + 1/2) / ny) is an exact
+    eigenvector with factor 1 - 4 Fo sin^2(pi k / 2 nx) - 4 Fo sin^2(pi l / 2 ny)."""
+    nx, ny, fo, steps = 80, 48, 0.2, 300
+    dx = 0.1
+    dt = fo * dx * dx
+    ld = np.longdouble
+    for k, l in ((1, 1), (3, 2), (5, 4)):
+        ci = np.cos(np.pi * k * (np.arange(nx) + 0.5) / nx)
+        cj = np.cos(np.pi * l * (np.arange(ny) + 0.5) / ny)
+        u0 = np.outer(cj, ci)
+        g = ld(1) - ld(4) * ld(fo) * np.sin(ld(np.pi) * k / (2 * nx)) ** 2 \
+            - ld(4) * ld(fo) * np.sin(ld(np.pi) * l / (2 * ny)) ** 2
+        u = oracle.heat2d(u0, dx, dt, 1.0, steps, bc=BC_MIRROR)
+        assert relerr(u, np.asarray(u0, dtype=ld) * g ** steps) <= 1e-12
+
+
+@pytest.mark.parametrize("bc", [BC_PERIODIC, BC_MIRROR])
+def test_heat2d_conserves_sum(bc):
+    """Periodic and insulated 2D heat conserve the total heat (no flux through walls)."""
+    p = inputs.heat2d_problem(nx=32, ny=20, noise=0.3)
+    u0 = p["u0"] + 0.5
+    u = oracle.heat2d(u0, p["dx"], p["dt"], p["alpha"], 500, bc=bc)
+    assert abs(u.sum() - u0.sum()) <= 1e-12 * np.abs(u0).sum() * 10
+
+
+@pytest.mark.parametrize("bc", [BC_PERIODIC, BC_MIRROR])
+def test_heat2d_matrix_power(bc):
+    """Brute force on a 5 x 3 grid: the one-step matrix built from the stencil definition,
+    raised to the 37th power, applied to a random state."""
+    nx, ny, fo, steps = 5, 3, 0.23, 37
+    u0 = inputs.rng(77).standard_normal((ny, nx))
+
+    def idx(q, n):
+        if 0 <= q < n:
+            return q
+        if bc == BC_PERIODIC:
+            return q % n
+        return -1 - q if q < 0 else 2 * n - 1 - q
+
+    A = np.zeros((nx * ny, nx * ny))
+    for j in range(ny):
+        for i in range(nx):
+            r = j * nx + i
+            A[r, r] += 1 - 4 * fo
+            for (ii, jj) in ((i - 1, j), (i + 1, j), (i, j - 1), (i, j + 1)):
+                A[r, idx(jj, ny) * nx + idx(ii, nx)] += fo
+    ref = (np.linalg.matrix_power(A, steps) @ u0.ravel()).reshape(ny, nx)
+    u = oracle.heat2d(u0, 1.0, fo, 1.0, steps, bc=bc)
+    assert relerr(u, ref) <= 1e-13
+
+
+def test_heat2d_reduces_to_1d():
+    """A field constant in y evolves as the 1D FTCS heat equation with the same Fo."""
+    p1 = inputs.heat_problem(n=96, r=0.2)
+    u2 = np.tile(p1["u0"], (16, 1))
+    u = oracle.heat2d(u2, p1["dx"], p1["dt"], p1["alpha"], 300)
+    ref = oracle.heat(p1["u0"], p1["dx"], p1["dt"], p1["alpha"], 300)
+    assert relerr(u, np.tile(ref, (16, 1))) <= 1e-13
+
+
+def test_heat2d_fp32_twin_and_threads():
+    """FP32 twin within 1e-5 of FP64 at 500 steps; results independent of the thread count."""
+    p64 = inputs.heat2d_problem(nx=64, ny=64)
+    p32 = inputs.heat2d_problem(nx=64, ny=64, dtype=np.float32)
+    a = oracle.heat2d(p64["u0"], p64["dx"], p64["dt"], p64["alpha"], 500)
+    b = oracle.heat2d(p32["u0"], p32["dx"], p32["dt"], p32["alpha"], 500)
+    assert b.dtype == np.float32 and relerr(b, a) <= 1e-5
+    c = oracle.heat2d(p64["u0"], p64["dx"], p64["dt"], p64["alpha"], 500, threads=4)
+    assert np.array_equal(a, c)
