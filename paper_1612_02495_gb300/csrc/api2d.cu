@@ -1,0 +1,357 @@
+// C-ABI runtime of the 2D swept solver (include/swept2d.h): plan, workspace
+// layout, launch sequence of the swept and classic paths, CUDA-graph caching.
+#include <stdio.h>
+#include <string.h>
+
+#include <functional>
+#include <map>
+#include <new>
+#include <string>
+
+#include "kernels2d.cuh"
+#include "swept2d.h"
+
+using swept2d::Geom2;
+
+struct swept2d_handle {
+  swept2d_config cfg;
+  Geom2 g;
+  int threads = 256;
+  size_t smem = 0;
+  int device = -1;
+  int value_bytes = 8;
+  double fo = 0.0;  // alpha dt / dx^2, in double
+  char* ws = nullptr;
+  size_t ws_bytes = 0, ws_bound = 0;
+  size_t off_s0 = 0, off_s1 = 0, off_b = 0, off_tmp = 0, off_status = 0;
+  cudaStream_t cap = nullptr;
+  std::map<std::string, cudaGraphExec_t> graphs;
+  std::string err;
+};
+
+namespace swept2d {
+// symbolic replay of the 2D launch sequence (check2d.cpp)
+bool check_schedule2d(const Geom2& g, int64_t nsteps, int64_t* computed, std::string* err);
+}  // namespace swept2d
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kSmemOptin = 232448;  // GB300 opt-in shared memory per block
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+swept_status fail(swept2d_handle* h, swept_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  return st;
+}
+swept_status cuda_fail(swept2d_handle* h, cudaError_t e, const char* where) {
+  return fail(h, SWEPT_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+int max_tile(int dtype) { return dtype == SWEPT_F64 ? 64 : 128; }
+bool tile_ok(int64_t nx, int64_t ny, int W, int dtype) {
+  return W >= 8 && W <= max_tile(dtype) && W % 4 == 0 && nx % W == 0 && ny % W == 0 && nx / W >= 2 && ny / W >= 2;
+}
+// default: 32 where it fits (the measured best at 2^20 points), else the largest legal W
+int choose_tile(int64_t nx, int64_t ny, int dtype) {
+  if (tile_ok(nx, ny, 32, dtype)) return 32;
+  for (int W = max_tile(dtype); W >= 8; W -= 4)
+    if (tile_ok(nx, ny, W, dtype)) return W;
+  return 0;
+}
+
+std::string key_of(const char* kind, const void* u, int64_t a) {
+  char buf[128];
+  snprintf(buf, sizeof buf, "%s:%p:%lld", kind, u, (long long)a);
+  return buf;
+}
+
+swept_status run_graph(swept2d_handle* h, const std::string& key, cudaStream_t user,
+                       const std::function<cudaError_t(cudaStream_t)>& issue) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(user, &cs);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamIsCapturing");
+  if (cs != cudaStreamCaptureStatusNone) {
+    e = issue(user);
+    return e == cudaSuccess ? SWEPT_OK : cuda_fail(h, e, "kernel launch");
+  }
+  auto it = h->graphs.find(key);
+  if (it == h->graphs.end()) {
+    e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamBeginCapture");
+    cudaError_t le = issue(h->cap);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(h->cap, &graph);
+    if (le != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(h, le, "kernel launch during capture");
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    it = h->graphs.emplace(key, exec).first;
+  }
+  e = cudaGraphLaunch(it->second, user);
+  return e == cudaSuccess ? SWEPT_OK : cuda_fail(h, e, "cudaGraphLaunch");
+}
+
+void drop_graphs(swept2d_handle* h) {
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+}
+
+template <typename T>
+cudaError_t prepare_t(size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(swept2d::k_pyr2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(swept2d::k_bridge2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(swept2d::k_octa2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return e;
+}
+
+swept_status ensure_device(swept2d_handle* h) {
+  if (h->device < 0) return fail(h, SWEPT_ECUDA, "no CUDA device was available when the handle was created");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaGetDevice");
+  if (dev != h->device) return fail(h, SWEPT_EINVAL, "current device differs from the handle's device");
+  if (!h->cap) {
+    if (h->smem > 48 * 1024) {
+      e = h->value_bytes == 8 ? prepare_t<double>(h->smem) : prepare_t<float>(h->smem);
+      if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)");
+    }
+    e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamCreateWithFlags");
+  }
+  return SWEPT_OK;
+}
+
+swept_status check_ready(swept2d_handle* h, void* u_dev, int64_t nsteps) {
+  if (!h) return SWEPT_EINVAL;
+  if (!u_dev || nsteps < 0) return fail(h, SWEPT_EINVAL, "u_dev is NULL or nsteps < 0");
+  if (!h->ws) return fail(h, SWEPT_ENOWORKSPACE, "no workspace bound (swept2d_bind_workspace)");
+  if (h->ws_bound < h->ws_bytes) return fail(h, SWEPT_ENOMEM_WORKSPACE, "bound workspace too small");
+  return ensure_device(h);
+}
+
+template <typename T>
+swept2d::Heat2dK<T> consts(const swept2d_handle* h) {
+  swept2d::Heat2dK<T> k;
+  k.fo = (T)h->fo;
+  k.c1 = (T)(1.0 - 4.0 * h->fo);
+  return k;
+}
+
+// launches [from, to) of for_each_launch2d
+template <typename T>
+cudaError_t issue_swept_t(swept2d_handle* h, T* u, int64_t n, int64_t from, int64_t to, cudaStream_t s) {
+  const Geom2& g = h->g;
+  const auto k = consts<T>(h);
+  T* S[2] = {(T*)(h->ws + h->off_s0), (T*)(h->ws + h->off_s1)};
+  T* B = (T*)(h->ws + h->off_b);
+  const unsigned tiles = (unsigned)(g.ntx * g.nty);
+  int64_t idx = 0;
+  cudaError_t err = cudaSuccess;
+  swept2d::for_each_launch2d(g, n, [&](int kind, int par, int mode, int hh, int64_t c) {
+    const int64_t i = idx++;
+    if (err != cudaSuccess || i < from || i >= to) return;
+    const int in = c >= 1 ? (int)((c - 1) & 1) : 0;
+    const int out = c >= 0 ? (int)(c & 1) : 1;
+    if (kind == swept2d::K_PYR)
+      swept2d::k_pyr2d<T><<<tiles, h->threads, h->smem, s>>>(g, k, u, S[c >= 0 ? out : 0], par, hh,
+                                                              mode == swept2d::M2_GAP);
+    else if (kind == swept2d::K_BRIDGE)
+      swept2d::k_bridge2d<T><<<2 * tiles, h->threads, h->smem, s>>>(g, k, u, S[in], B, par, hh,
+                                                                     mode == swept2d::M2_GAP);
+    else
+      swept2d::k_octa2d<T><<<tiles, h->threads, h->smem, s>>>(g, k, u, S[in], S[out], B, par, mode, hh);
+    err = cudaGetLastError();
+  });
+  return err;
+}
+
+cudaError_t issue_swept(swept2d_handle* h, void* u, int64_t n, int64_t from, int64_t to, cudaStream_t s) {
+  return h->value_bytes == 8 ? issue_swept_t<double>(h, (double*)u, n, from, to, s)
+                             : issue_swept_t<float>(h, (float*)u, n, from, to, s);
+}
+
+// classic steps [k0, k1): step m reads u (m even) or the second array and
+// writes the other; an odd total leaves the result in u by a final copy
+template <typename T>
+cudaError_t issue_classic_t(swept2d_handle* h, T* u, int64_t k0, int64_t k1, int64_t total, cudaStream_t s) {
+  const Geom2& g = h->g;
+  const auto k = consts<T>(h);
+  T* tmp = (T*)(h->ws + h->off_tmp);
+  const dim3 grid((unsigned)((g.nx + 255) / 256), (unsigned)g.ny);
+  for (int64_t m = k0; m < k1; ++m) {
+    const T* in = (m & 1) ? tmp : u;
+    T* out = (m & 1) ? u : tmp;
+    swept2d::k_classic2d<T><<<grid, 256, 0, s>>>(g.nx, g.ny, k, in, out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (k1 == total && (total & 1))
+    return cudaMemcpyAsync(u, tmp, (size_t)(g.nx * g.ny) * sizeof(T), cudaMemcpyDeviceToDevice, s);
+  return cudaSuccess;
+}
+
+cudaError_t issue_classic(swept2d_handle* h, void* u, int64_t k0, int64_t k1, int64_t total, cudaStream_t s) {
+  return h->value_bytes == 8 ? issue_classic_t<double>(h, (double*)u, k0, k1, total, s)
+                             : issue_classic_t<float>(h, (float*)u, k0, k1, total, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+swept_status swept2d_init(const swept2d_config* cfg, swept2d_handle** out) {
+  if (!cfg || !out) return SWEPT_EINVAL;
+  *out = nullptr;
+  if (cfg->dtype != SWEPT_F32 && cfg->dtype != SWEPT_F64) return SWEPT_EINVAL;
+  if (cfg->bc != SWEPT_BC_PERIODIC) return SWEPT_EINVAL;
+  if (!(cfg->dx > 0) || !(cfg->dt > 0) || !(cfg->alpha > 0)) return SWEPT_EINVAL;
+  if (cfg->nx < 16 || cfg->ny < 16 || cfg->ny > 65535) return SWEPT_EINVAL;
+  const int W = cfg->tile_w > 0 ? cfg->tile_w : choose_tile(cfg->nx, cfg->ny, cfg->dtype);
+  if (W <= 0 || !tile_ok(cfg->nx, cfg->ny, W, cfg->dtype)) return SWEPT_EINVAL;
+  const int th = cfg->threads > 0 ? cfg->threads : 256;
+  if (th < 32 || th > 1024 || th % 32 != 0) return SWEPT_EINVAL;
+  swept2d_handle* h = new (std::nothrow) swept2d_handle();
+  if (!h) return SWEPT_EINVAL;
+  h->cfg = *cfg;
+  h->threads = th;
+  h->value_bytes = cfg->dtype == SWEPT_F64 ? 8 : 4;
+  h->fo = cfg->alpha * cfg->dt / (cfg->dx * cfg->dx);
+  Geom2& g = h->g;
+  g.nx = cfg->nx;
+  g.ny = cfg->ny;
+  g.W = W;
+  g.R = 1;
+  g.h = W / 2;
+  g.M = W + 2;
+  g.ntx = cfg->nx / W;
+  g.nty = cfg->ny / W;
+  g.Ph = swept2d::strip_off(g, g.h);
+  g.Bh = swept2d::band_off(g, g.h);
+  g.Es = 4 * 2 * g.R * g.Ph;
+  g.Eb = 2 * 2 * g.R * g.Bh;
+  h->smem = (size_t)2 * g.M * g.M * h->value_bytes;
+  if (h->smem > (size_t)kSmemOptin) {
+    delete h;
+    return SWEPT_EINVAL;
+  }
+  const size_t vb = (size_t)h->value_bytes;
+  const size_t strips = align_up((size_t)(g.ntx * g.nty * g.Es) * vb);
+  h->off_s0 = 0;
+  h->off_s1 = strips;
+  h->off_b = 2 * strips;
+  h->off_tmp = h->off_b + align_up((size_t)(2 * g.ntx * g.nty * g.Eb) * vb);
+  h->off_status = h->off_tmp + align_up((size_t)(g.nx * g.ny) * vb);
+  h->ws_bytes = h->off_status + kAlign;
+  int dev = -1;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    int n = 0;
+    if (cudaGetDeviceCount(&n) == cudaSuccess && n > 0) h->device = dev;
+  }
+  cudaGetLastError();  // clear a no-device error
+  *out = h;
+  return SWEPT_OK;
+}
+
+swept_status swept2d_workspace_size(const swept2d_handle* h, size_t* bytes) {
+  if (!h || !bytes) return SWEPT_EINVAL;
+  *bytes = h->ws_bytes;
+  return SWEPT_OK;
+}
+
+swept_status swept2d_bind_workspace(swept2d_handle* h, void* ws_dev, size_t bytes) {
+  if (!h) return SWEPT_EINVAL;
+  if (!ws_dev || ((uintptr_t)ws_dev % kAlign) != 0)
+    return fail(h, SWEPT_EINVAL, "workspace NULL or not 256-byte aligned");
+  if (bytes < h->ws_bytes) return fail(h, SWEPT_ENOMEM_WORKSPACE, "workspace smaller than swept2d_workspace_size()");
+  swept_status st = ensure_device(h);
+  if (st != SWEPT_OK) return st;
+  drop_graphs(h);
+  h->ws = (char*)ws_dev;
+  h->ws_bound = bytes;
+  return SWEPT_OK;
+}
+
+swept_status swept2d_step_n(swept2d_handle* h, void* u_dev, int64_t nsteps, void* stream) {
+  swept_status st = check_ready(h, u_dev, nsteps);
+  if (st != SWEPT_OK || nsteps == 0) return st;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const Geom2& g = h->g;
+  const int64_t L = swept2d::launch_count2d(g, nsteps);
+  const int64_t q = nsteps / g.h;
+  const int64_t K = 256;  // half cycles per cached body graph (even: the body repeats with the tiling parity)
+  const int64_t reps = q > 1 ? (q - 1) / K : 0;
+  if (reps == 0)
+    return run_graph(h, key_of("swept2d", u_dev, nsteps), s,
+                     [&](cudaStream_t cs) { return issue_swept(h, u_dev, nsteps, 0, L, cs); });
+  // head (the first pyramid), reps bodies of K half cycles (launches 1 .. 2K),
+  // tail (the rest, including the last octahedron and the remainder)
+  st = run_graph(h, key_of("swept2d_head", u_dev, 0), s,
+                 [&](cudaStream_t cs) { return issue_swept(h, u_dev, nsteps, 0, 1, cs); });
+  for (int64_t r = 0; r < reps && st == SWEPT_OK; ++r)
+    st = run_graph(h, key_of("swept2d_body", nullptr, K), s,
+                   [&](cudaStream_t cs) { return issue_swept(h, u_dev, nsteps, 1, 1 + 2 * K, cs); });
+  if (st != SWEPT_OK) return st;
+  const int64_t t0 = 1 + 2 * K * reps;
+  return run_graph(h, key_of("swept2d_tail", u_dev, nsteps), s,
+                   [&](cudaStream_t cs) { return issue_swept(h, u_dev, nsteps, t0, L, cs); });
+}
+
+swept_status classic2d_step_n(swept2d_handle* h, void* u_dev, int64_t nsteps, void* stream) {
+  swept_status st = check_ready(h, u_dev, nsteps);
+  if (st != SWEPT_OK || nsteps == 0) return st;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const int64_t kBody = 512;  // even, so a body starts and ends in u
+  const int64_t reps = nsteps > 2 * kBody ? nsteps / kBody - 1 : 0;
+  for (int64_t r = 0; r < reps && st == SWEPT_OK; ++r)
+    st = run_graph(h, key_of("classic2d_body", u_dev, kBody), s,
+                   [&](cudaStream_t cs) { return issue_classic(h, u_dev, 0, kBody, kBody, cs); });
+  if (st != SWEPT_OK) return st;
+  const int64_t rest = nsteps - reps * kBody;
+  return run_graph(h, key_of("classic2d_tail", u_dev, rest), s,
+                   [&](cudaStream_t cs) { return issue_classic(h, u_dev, 0, rest, rest, cs); });
+}
+
+swept_status swept2d_get_plan(const swept2d_handle* h, swept2d_plan_info* out) {
+  if (!h || !out) return SWEPT_EINVAL;
+  memset(out, 0, sizeof(*out));
+  out->tile_w = h->g.W;
+  out->threads = h->threads;
+  out->half_cycle = h->g.h;
+  out->tiles_x = h->g.ntx;
+  out->tiles_y = h->g.nty;
+  out->smem_bytes = (int64_t)h->smem;
+  out->workspace_bytes = (int64_t)h->ws_bytes;
+  return SWEPT_OK;
+}
+
+swept_status swept2d_check_schedule(swept2d_handle* h, int64_t nsteps, int64_t* computed) {
+  if (!h || nsteps < 0) return SWEPT_EINVAL;
+  std::string err;
+  if ((double)(nsteps + 1) * (double)(h->g.nx * h->g.ny) > 2e8)
+    return fail(h, SWEPT_EINVAL, "schedule check too large ((nsteps + 1) * nx * ny > 2e8)");
+  if (!swept2d::check_schedule2d(h->g, nsteps, computed, &err)) return fail(h, SWEPT_EDEVICE, err);
+  return SWEPT_OK;
+}
+
+swept_status swept2d_last_error(const swept2d_handle* h, char* buf, size_t len) {
+  if (!h || !buf || len == 0) return SWEPT_EINVAL;
+  snprintf(buf, len, "%s", h->err.c_str());
+  return SWEPT_OK;
+}
+
+void swept2d_free(swept2d_handle* h) {
+  if (!h) return;
+  drop_graphs(h);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  delete h;
+}
+
+}  // extern "C"

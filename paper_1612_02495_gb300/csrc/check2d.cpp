@@ -1,0 +1,233 @@
+// Host-side symbolic replay of the 2D swept launch sequence
+// (swept2d_check_schedule).
+//
+// Runs the same phase code as the kernels (swept2d.cuh) over every block, with
+// buffers that hold (point, level) tags instead of values, and checks:
+//   - a point of level L is computed only when its five stencil inputs hold
+//     level L - 1 of the right grid points, found from the periodic grid
+//     itself (independently of the window arithmetic);
+//   - every point of every level 1..n is computed exactly once;
+//   - blocks of one launch never touch a global location another block of
+//     the same launch writes;
+//   - every window index stays inside the window and every strip and band
+//     index inside its buffer;
+//   - at the end the state holds level n at every point.
+#include <stdio.h>
+
+#include <string>
+#include <vector>
+
+#include "swept2d.cuh"
+
+namespace swept2d {
+namespace {
+
+struct Tag {
+  int64_t p = -1;    // grid point y * nx + x
+  int64_t lvl = -1;  // level
+};
+
+struct Access {
+  int64_t stamp = -1;
+  int64_t writer = -1;
+  int64_t reader = -1;  // -2: read by several blocks
+};
+
+struct Sim2 {
+  Geom2 g;
+  int64_t n = 0;
+  std::vector<Tag> u, s[2], b;
+  std::vector<Access> au, as[2], ab;
+  std::vector<uint8_t> count;  // (n + 1) * nx * ny
+  int64_t stamp = 0;
+  int64_t computed = 0;
+  std::string err;
+
+  void fail(const std::string& m) {
+    if (err.empty()) err = m;
+  }
+  void note(std::vector<Access>& a, size_t i, int64_t block, bool write, const char* what) {
+    Access& x = a[i];
+    if (x.stamp != stamp) x = Access{stamp, -1, -1};
+    char m[160];
+    if (write) {
+      if ((x.writer != -1 && x.writer != block) || (x.reader != -1 && x.reader != block)) {
+        snprintf(m, sizeof m, "race on %s[%zu] between blocks in launch %lld", what, i, (long long)stamp);
+        fail(m);
+      }
+      x.writer = block;
+    } else {
+      if (x.writer != -1 && x.writer != block) {
+        snprintf(m, sizeof m, "block %lld reads %s[%zu] written by block %lld in the same launch", (long long)block,
+                 what, i, (long long)x.writer);
+        fail(m);
+      }
+      x.reader = (x.reader == -1 || x.reader == block) ? block : -2;
+    }
+  }
+};
+
+struct Host2Ctx {
+  Sim2& sim;
+  const Geom2& g;
+  int64_t block;
+  int64_t base_level;  // absolute level of the launch's local level 0
+  int sin, sout;
+  std::vector<Tag> w;  // two rows of M x M tags
+
+  Host2Ctx(Sim2& s, int64_t b, int64_t base, int si, int so)
+      : sim(s), g(s.g), block(b), base_level(base), sin(si), sout(so), w((size_t)2 * s.g.M * s.g.M) {}
+
+  template <class F>
+  void for_grid(int nout, int nin, F&& f) {
+    for (int o = 0; o < nout; ++o)
+      for (int i = 0; i < nin; ++i) f(o, i);
+  }
+  void sync() {}
+  Tag& cell(int r, int lx, int ly) {
+    if (lx < 0 || lx >= g.M || ly < 0 || ly >= g.M) {
+      sim.fail("window index out of range");
+      static Tag dummy;
+      return dummy;
+    }
+    return w[((size_t)r * g.M + ly) * g.M + lx];
+  }
+  int64_t gp(int64_t gx, int64_t gy) const { return wrap_n(gy, g.ny) * g.nx + wrap_n(gx, g.nx); }
+  void load_u(int r, int lx, int ly, int64_t gx, int64_t gy) {
+    const size_t i = (size_t)gp(gx, gy);
+    sim.note(sim.au, i, block, false, "u");
+    cell(r, lx, ly) = sim.u[i];
+  }
+  void store_u(int r, int lx, int ly, int64_t gx, int64_t gy) {
+    const size_t i = (size_t)gp(gx, gy);
+    sim.note(sim.au, i, block, true, "u");
+    const Tag t = cell(r, lx, ly);
+    if (t.p != (int64_t)i) sim.fail("store_u writes the value of another point");
+    sim.u[i] = t;
+  }
+  void load_strip(int r, int lx, int ly, int64_t e) {
+    if (e < 0 || (size_t)e >= sim.s[sin].size()) return sim.fail("strip index out of range");
+    sim.note(sim.as[sin], (size_t)e, block, false, "strips");
+    cell(r, lx, ly) = sim.s[sin][(size_t)e];
+  }
+  void store_strip(int r, int lx, int ly, int64_t e) {
+    if (e < 0 || (size_t)e >= sim.s[sout].size()) return sim.fail("strip index out of range");
+    sim.note(sim.as[sout], (size_t)e, block, true, "strips");
+    sim.s[sout][(size_t)e] = cell(r, lx, ly);
+  }
+  void load_band(int r, int lx, int ly, int64_t e) {
+    if (e < 0 || (size_t)e >= sim.b.size()) return sim.fail("band index out of range");
+    sim.note(sim.ab, (size_t)e, block, false, "bands");
+    cell(r, lx, ly) = sim.b[(size_t)e];
+  }
+  void store_band(int r, int lx, int ly, int64_t e) {
+    if (e < 0 || (size_t)e >= sim.b.size()) return sim.fail("band index out of range");
+    sim.note(sim.ab, (size_t)e, block, true, "bands");
+    sim.b[(size_t)e] = cell(r, lx, ly);
+  }
+  void level(int s, int base, int x0, int x1, int y0, int y1, int64_t ox, int64_t oy) {
+    const int64_t L = base_level + base + s;
+    const int row = s & 1;
+    static const int dxs[5] = {0, -1, 1, 0, 0}, dys[5] = {0, 0, 0, -1, 1};
+    char m[220];
+    for (int ly = y0; ly < y1; ++ly)
+      for (int lx = x0; lx < x1; ++lx) {
+        const int64_t gx = ox + lx, gy = oy + ly;
+        for (int d = 0; d < 5; ++d) {
+          const Tag t = cell(row ^ 1, lx + dxs[d], ly + dys[d]);
+          const int64_t want = gp(gx + dxs[d], gy + dys[d]);
+          if (t.p != want || t.lvl != L - 1) {
+            snprintf(m, sizeof m,
+                     "block %lld level %lld point (%lld, %lld): input (%d, %d) holds (point %lld, level %lld), "
+                     "expected (%lld, %lld)",
+                     (long long)block, (long long)L, (long long)wrap_n(gx, g.nx), (long long)wrap_n(gy, g.ny),
+                     dxs[d], dys[d], (long long)t.p, (long long)t.lvl, (long long)want, (long long)(L - 1));
+            return sim.fail(m);
+          }
+        }
+      }
+    for (int ly = y0; ly < y1; ++ly)
+      for (int lx = x0; lx < x1; ++lx) {
+        const int64_t p = gp(ox + lx, oy + ly);
+        cell(row, lx, ly) = Tag{p, L};
+        if (L >= 1 && L <= sim.n) {
+          uint8_t& c = sim.count[(size_t)L * g.nx * g.ny + (size_t)p];
+          if (c < 255) ++c;
+        }
+        ++sim.computed;
+      }
+  }
+};
+
+}  // namespace
+
+bool check_schedule2d(const Geom2& g, int64_t n, int64_t* computed, std::string* err) {
+  Sim2 sim;
+  sim.g = g;
+  sim.n = n;
+  const int64_t np = g.nx * g.ny;
+  sim.u.resize((size_t)np);
+  for (int64_t p = 0; p < np; ++p) sim.u[(size_t)p] = Tag{p, 0};
+  for (int i = 0; i < 2; ++i) {
+    sim.s[i].assign((size_t)(g.ntx * g.nty * g.Es), Tag{});
+    sim.as[i].assign(sim.s[i].size(), Access{});
+  }
+  sim.b.assign((size_t)(2 * g.ntx * g.nty * g.Eb), Tag{});
+  sim.ab.assign(sim.b.size(), Access{});
+  sim.au.assign((size_t)np, Access{});
+  sim.count.assign((size_t)(n + 1) * (size_t)np, 0);
+  const int64_t q = n / g.h;
+  const int64_t tiles = g.ntx * g.nty;
+  for_each_launch2d(g, n, [&](int kind, int par, int mode, int hh, int64_t c) {
+    ++sim.stamp;
+    const int64_t base = c >= 1 ? (c - 1) * (int64_t)g.h : (c == 0 ? 0 : q * (int64_t)g.h);
+    const int in = c >= 1 ? (int)((c - 1) & 1) : 0;
+    const int out = c >= 0 ? (int)(c & 1) : 1;
+    if (kind == K_PYR) {
+      for (int64_t b = 0; b < tiles && sim.err.empty(); ++b) {
+        Host2Ctx cx(sim, b, base, 0, c >= 0 ? out : 0);
+        run_pyr(cx, g, b % g.ntx, b / g.ntx, par, hh, mode == M2_GAP);
+      }
+    } else if (kind == K_BRIDGE) {
+      for (int64_t b = 0; b < 2 * tiles && sim.err.empty(); ++b) {
+        Host2Ctx cx(sim, b, base, in, out);
+        run_bridge(cx, g, b, par, hh, mode == M2_GAP);
+      }
+    } else {
+      for (int64_t b = 0; b < tiles && sim.err.empty(); ++b) {
+        Host2Ctx cx(sim, b, base, in, out);
+        run_octa(cx, g, b % g.ntx, b / g.ntx, par, mode, hh);
+      }
+    }
+  });
+  if (sim.err.empty())
+    for (int64_t p = 0; p < np; ++p) {
+      const Tag t = sim.u[(size_t)p];
+      if (t.p != p || t.lvl != n) {
+        char m[160];
+        snprintf(m, sizeof m, "final state at point %lld holds (point %lld, level %lld), expected level %lld",
+                 (long long)p, (long long)t.p, (long long)t.lvl, (long long)n);
+        sim.fail(m);
+        break;
+      }
+    }
+  if (sim.err.empty())
+    for (int64_t L = 1; L <= n && sim.err.empty(); ++L)
+      for (int64_t p = 0; p < np; ++p) {
+        const uint8_t c = sim.count[(size_t)L * np + (size_t)p];
+        if (c != 1) {
+          char m[160];
+          snprintf(m, sizeof m, "point %lld of level %lld computed %d times", (long long)p, (long long)L, (int)c);
+          sim.fail(m);
+          break;
+        }
+      }
+  if (computed) *computed = sim.computed;
+  if (!sim.err.empty()) {
+    if (err) *err = sim.err;
+    return false;
+  }
+  return true;
+}
+
+}  // namespace swept2d

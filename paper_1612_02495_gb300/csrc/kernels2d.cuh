@@ -1,0 +1,118 @@
+// CUDA kernels of the 2D swept decomposition (swept2d.cuh) and the classic
+// one-launch-per-step 2D kernel, for the 2D FTCS heat equation
+//   T' = fma(Fo, (T_W + T_E) + (T_S + T_N), c1 T),  c1 = 1 - 4 Fo,
+// the 2D extension of Eq. HeatDisc, evaluated in this order everywhere.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ops.cuh"
+#include "swept2d.cuh"
+
+namespace swept2d {
+
+using swept::add_rn;
+using swept::fma_rn;
+using swept::mul_rn;
+
+template <typename T>
+struct Heat2dK {
+  T fo, c1;
+};
+
+// the 5-point update of window point c (row stride M)
+template <typename T>
+__device__ __forceinline__ T heat2d_point(const T* c, int M, const Heat2dK<T>& k) {
+  const T sx = add_rn(c[-1], c[1]);
+  const T sy = add_rn(c[-M], c[M]);
+  return fma_rn(k.fo, add_rn(sx, sy), mul_rn(k.c1, c[0]));
+}
+
+// Device context of one block: the two level rows of its (W + 2R)^2 window in
+// shared memory; rows of the window are spread over warps, points of a row
+// over lanes.
+template <typename T>
+struct Dev2Ctx {
+  T* sm;
+  Geom2 g;
+  Heat2dK<T> k;
+  T* u;
+  const T* s_in;
+  T* s_out;
+  const T* b_in;
+  T* b_out;
+
+  __device__ __forceinline__ T& at(int r, int lx, int ly) { return sm[((int64_t)r * g.M + ly) * g.M + lx]; }
+  __device__ __forceinline__ int64_t gidx(int64_t gx, int64_t gy) const {
+    return wrap_n(gy, g.ny) * g.nx + wrap_n(gx, g.nx);
+  }
+  template <class F>
+  __device__ __forceinline__ void for_grid(int nout, int nin, F&& f) {
+    const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31u), nw = (int)(blockDim.x >> 5);
+    for (int o = warp; o < nout; o += nw)
+      for (int i = lane; i < nin; i += 32) f(o, i);
+  }
+  __device__ __forceinline__ void sync() { __syncthreads(); }
+  __device__ __forceinline__ void load_u(int r, int lx, int ly, int64_t gx, int64_t gy) {
+    at(r, lx, ly) = u[gidx(gx, gy)];
+  }
+  __device__ __forceinline__ void store_u(int r, int lx, int ly, int64_t gx, int64_t gy) {
+    u[gidx(gx, gy)] = at(r, lx, ly);
+  }
+  __device__ __forceinline__ void load_strip(int r, int lx, int ly, int64_t e) { at(r, lx, ly) = s_in[e]; }
+  __device__ __forceinline__ void store_strip(int r, int lx, int ly, int64_t e) { s_out[e] = at(r, lx, ly); }
+  __device__ __forceinline__ void load_band(int r, int lx, int ly, int64_t e) { at(r, lx, ly) = b_in[e]; }
+  __device__ __forceinline__ void store_band(int r, int lx, int ly, int64_t e) { b_out[e] = at(r, lx, ly); }
+  // level s on the local rectangle [x0, x1) x [y0, y1): row s & 1 from row (s - 1) & 1
+  __device__ __forceinline__ void level(int s, int, int x0, int x1, int y0, int y1, int64_t, int64_t) {
+    const int M = g.M;
+    const T* in = sm + (int64_t)((s & 1) ^ 1) * M * M;
+    T* out = sm + (int64_t)(s & 1) * M * M;
+    const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31u), nw = (int)(blockDim.x >> 5);
+    for (int ly = y0 + warp; ly < y1; ly += nw)
+      for (int lx = x0 + lane; lx < x1; lx += 32) out[ly * M + lx] = heat2d_point<T>(in + ly * M + lx, M, k);
+    __syncthreads();
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_pyr2d(Geom2 g, Heat2dK<T> k, T* u, T* s_out, int par, int hh,
+                                                 int write_top) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Dev2Ctx<T> cx{reinterpret_cast<T*>(smraw), g, k, u, nullptr, s_out, nullptr, nullptr};
+  const int64_t b = blockIdx.x;
+  run_pyr(cx, g, b % g.ntx, b / g.ntx, par, hh, write_top != 0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_bridge2d(Geom2 g, Heat2dK<T> k, T* u, const T* s_in, T* b_out, int par,
+                                                    int hh, int write_top) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Dev2Ctx<T> cx{reinterpret_cast<T*>(smraw), g, k, u, s_in, nullptr, nullptr, b_out};
+  run_bridge(cx, g, (int64_t)blockIdx.x, par, hh, write_top != 0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_octa2d(Geom2 g, Heat2dK<T> k, T* u, const T* s_in, T* s_out,
+                                                  const T* b_in, int odd, int mode, int hh) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Dev2Ctx<T> cx{reinterpret_cast<T*>(smraw), g, k, u, s_in, s_out, b_in, nullptr};
+  const int64_t b = blockIdx.x;
+  run_octa(cx, g, b % g.ntx, b / g.ntx, odd, mode, hh);
+}
+
+// classic: one step of the whole grid, global memory in and out (periodic)
+template <typename T>
+__global__ void __launch_bounds__(256) k_classic2d(int64_t nx, int64_t ny, Heat2dK<T> k, const T* __restrict__ in,
+                                                   T* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (i >= nx) return;
+  const int64_t iw = i == 0 ? nx - 1 : i - 1, ie = i == nx - 1 ? 0 : i + 1;
+  const int64_t js = j == 0 ? ny - 1 : j - 1, jn = j == ny - 1 ? 0 : j + 1;
+  const T sx = add_rn(in[j * nx + iw], in[j * nx + ie]);
+  const T sy = add_rn(in[js * nx + i], in[jn * nx + i]);
+  out[j * nx + i] = fma_rn(k.fo, add_rn(sx, sy), mul_rn(k.c1, in[j * nx + i]));
+}
+
+}  // namespace swept2d

@@ -1,0 +1,270 @@
+// Two-dimensional swept decomposition: geometry, pass phases and launch
+// sequence, shared by the CUDA kernels and the host-side schedule checker.
+//
+// The paper decomposes 1D problems and names two dimensions as future work
+// (Section "Conclusion").  This is that extension for a 2D stencil of radius R
+// on a periodic nx x ny grid of W x W tiles, h = W / (2R) levels per half
+// cycle.  At level s every point falls in exactly one of four regions, by
+// its distances dx, dy to the nearest tile boundary line of the current tiling:
+//   pyramid   dx >= R s and dy >= R s   (the tile's shrinking square)
+//   x-bridge  dx <  R s and dy >= R s   (grows across a vertical boundary,
+//                                        shrinks along it)
+//   y-bridge  dx >= R s and dy <  R s
+//   corner    dx <  R s and dy <  R s   (the square growing around a corner)
+// A pyramid needs only itself, a bridge its two pyramids and itself, a corner
+// everything around it.  So a half cycle runs in two launches:
+//   BRIDGE: every x- and y-bridge from the pyramids' side strips;
+//   OCTA:   every corner square grown from the pyramids' corner patches and
+//           the bridges' end bands up to a full tile of the half-shifted
+//           tiling, then (like the 1D diamond) shrunk as that tile's pyramid,
+//           exporting its side strips for the next BRIDGE.
+// The first launch is a plain pyramid (PYR) of each tile.  The last OCTA
+// writes its completed tile (level h) back to the state.  A remainder of
+// rem < h levels runs PYR, BRIDGE and OCTA truncated at rem, each writing its
+// level-rem region (the four regions of level rem partition the grid).
+//
+// Each block holds an (W + 2R)^2 window of two level rows (even levels in
+// row 0, odd levels in row 1), as in the 1D two-row buffer.  Exchange data:
+//   strips  per tile and level s < h, its four 2R-wide side strips of length
+//           W - 2Rs (sides: 0 left, 1 right, 2 bottom, 3 top), two buffers
+//           used in turn (an OCTA reads one and writes the other);
+//   bands   per bridge and level s < h, its two 2R-wide end bands of length
+//           2Rs (end 0 at the low end of its shrinking axis, 1 at the high end).
+#pragma once
+#include <stdint.h>
+
+#include "swept_geom.cuh"
+
+namespace swept2d {
+
+using swept::wrap_n;
+
+enum Kind2 : int { K_PYR = 0, K_BRIDGE = 1, K_OCTA = 2 };
+// FULL: a complete pass that exports; DOWN: the last OCTA, writes its tile;
+// GAP: a remainder pass, writes its level-hh region
+enum Mode2 : int { M2_FULL = 0, M2_DOWN = 1, M2_GAP = 2 };
+
+struct Geom2 {
+  int64_t nx, ny;    // grid points along x (fastest) and y
+  int64_t ntx, nty;  // tiles along x and y
+  int W;             // tile width
+  int R;             // stencil radius
+  int h;             // W / (2R)
+  int M;             // W + 2R: window width
+  int64_t Ph;        // sum over s < h of the strip length W - 2Rs
+  int64_t Bh;        // sum over s < h of the band length 2Rs
+  int64_t Es;        // values per tile in a strip buffer: 4 sides * 2R * Ph
+  int64_t Eb;        // values per bridge in the band buffer: 2 ends * 2R * Bh
+};
+
+SW_HD int strip_len(const Geom2& g, int s) { return g.W - 2 * g.R * s; }
+SW_HD int64_t strip_off(const Geom2& g, int s) { return (int64_t)s * g.W - (int64_t)g.R * s * (s - 1); }
+SW_HD int64_t strip_index(const Geom2& g, int64_t tile, int side, int s, int k, int p) {
+  return tile * g.Es + (int64_t)side * (2 * g.R) * g.Ph + (int64_t)(2 * g.R) * strip_off(g, s) +
+         (int64_t)k * strip_len(g, s) + p;
+}
+SW_HD int64_t band_off(const Geom2& g, int s) { return (int64_t)g.R * s * (s - 1); }
+SW_HD int64_t band_index(const Geom2& g, int64_t bridge, int end, int s, int k, int p) {
+  return bridge * g.Eb + (int64_t)end * (2 * g.R) * g.Bh + (int64_t)(2 * g.R) * band_off(g, s) +
+         (int64_t)k * (2 * g.R * s) + p;
+}
+SW_HD int64_t tile_id(const Geom2& g, int64_t tx, int64_t ty) { return wrap_n(ty, g.nty) * g.ntx + wrap_n(tx, g.ntx); }
+// x-bridge between tiles (tx, ty) and (tx+1, ty); y-bridge between (tx, ty) and (tx, ty+1)
+SW_HD int64_t xbridge_id(const Geom2& g, int64_t tx, int64_t ty) { return tile_id(g, tx, ty); }
+SW_HD int64_t ybridge_id(const Geom2& g, int64_t tx, int64_t ty) { return g.ntx * g.nty + tile_id(g, tx, ty); }
+
+// Export the four side strips of levels 0..hh-1 of the pyramid whose tile sits
+// at local [R, W + R)^2 (level s in row s & 1 on [R + Rs, W + R - Rs)^2).
+template <class Cx>
+SW_HD void export_strips(Cx& cx, const Geom2& g, int64_t tile, int hh) {
+  const int R = g.R, W = g.W;
+  cx.for_grid(4 * 2 * R * hh, W, [&](int o, int p) {
+    const int s = o % hh;
+    const int rest = o / hh;
+    const int k = rest % (2 * R);
+    const int side = rest / (2 * R);
+    if (p >= strip_len(g, s)) return;
+    const int across = side == 0 || side == 2 ? R + R * s + k : W - R - R * s + k;
+    const int along = R + R * s + p;
+    const int lx = side < 2 ? across : along;
+    const int ly = side < 2 ? along : across;
+    cx.store_strip(s & 1, lx, ly, strip_index(g, tile, side, s, k, p));
+  });
+}
+
+// Pyramid of tile (tx, ty) of the tiling with offset par * W/2: levels 1..hh,
+// strips of levels 0..hh-1; with write_top, level hh written back (remainder).
+template <class Cx>
+SW_HD void run_pyr(Cx& cx, const Geom2& g, int64_t tx, int64_t ty, int par, int hh, bool write_top) {
+  const int R = g.R, W = g.W;
+  const int64_t X0 = par * (W / 2) + tx * W, Y0 = par * (W / 2) + ty * W;
+  const int64_t ox = X0 - R, oy = Y0 - R;
+  cx.for_grid(W, W, [&](int b, int a) { cx.load_u(0, R + a, R + b, X0 + a, Y0 + b); });
+  cx.sync();
+  for (int s = 1; s <= hh; ++s) cx.level(s, 0, R + R * s, W + R - R * s, R + R * s, W + R - R * s, ox, oy);
+  export_strips(cx, g, tile_id(g, tx, ty), hh);
+  if (write_top) {
+    const int lo = R + R * hh, w = W - 2 * R * hh;
+    if (w > 0) cx.for_grid(w, w, [&](int b, int a) { cx.store_u(hh & 1, lo + a, lo + b, ox + lo + a, oy + lo + b); });
+  }
+}
+
+// Bridge `bid` (x-bridges first, then y-bridges) of the tiling with offset
+// par * W/2: the two pyramids' facing strips inserted, levels 1..hh grown
+// across the boundary and shrunk along it, end bands of levels 0..hh-1
+// exported; with write_top, level hh written back (remainder).
+template <class Cx>
+SW_HD void run_bridge(Cx& cx, const Geom2& g, int64_t bid, int par, int hh, bool write_top) {
+  const int R = g.R, W = g.W, half = W / 2;
+  const bool ydir = bid >= g.ntx * g.nty;
+  const int64_t t = ydir ? bid - g.ntx * g.nty : bid;
+  const int64_t tx = t % g.ntx, ty = t / g.ntx;
+  const int64_t o = par * half;
+  // window origin; local (u, v) = (grow-axis, shrink-axis) coordinates
+  const int64_t ox = ydir ? o + tx * W - R : o + (tx + 1) * W - half - R;
+  const int64_t oy = ydir ? o + (ty + 1) * W - half - R : o + ty * W - R;
+  const int64_t lo_tile = tile_id(g, tx, ty);
+  const int64_t hi_tile = ydir ? tile_id(g, tx, ty + 1) : tile_id(g, tx + 1, ty);
+  // strips: the low tile's high side (1 right / 3 top), the high tile's low side (0 / 2)
+  cx.for_grid(2 * 2 * R * hh, W, [&](int oo, int p) {
+    const int s = oo % hh;
+    const int rest = oo / hh;
+    const int k = rest % (2 * R);
+    const int which = rest / (2 * R);
+    if (p >= strip_len(g, s)) return;
+    const int gpos = which == 0 ? half - R - R * s + k : half + R + R * s + k;  // grow axis
+    const int spos = R + R * s + p;                                             // shrink axis
+    const int side = which == 0 ? (ydir ? 3 : 1) : (ydir ? 2 : 0);
+    const int64_t e = strip_index(g, which == 0 ? lo_tile : hi_tile, side, s, k, p);
+    if (ydir)
+      cx.load_strip(s & 1, spos, gpos, e);
+    else
+      cx.load_strip(s & 1, gpos, spos, e);
+  });
+  cx.sync();
+  for (int s = 1; s <= hh; ++s) {
+    const int g0 = half + R - R * s, g1 = half + R + R * s, s0 = R + R * s, s1 = W + R - R * s;
+    if (ydir)
+      cx.level(s, 0, s0, s1, g0, g1, ox, oy);
+    else
+      cx.level(s, 0, g0, g1, s0, s1, ox, oy);
+  }
+  const int64_t b = ydir ? ybridge_id(g, tx, ty) : xbridge_id(g, tx, ty);
+  cx.for_grid(2 * 2 * R * hh, 2 * R * hh, [&](int oo, int p) {
+    const int s = oo % hh;
+    const int rest = oo / hh;
+    const int k = rest % (2 * R);
+    const int end = rest / (2 * R);
+    if (p >= 2 * R * s) return;
+    const int gpos = half + R - R * s + p;
+    const int spos = end == 0 ? R + R * s + k : W - R - R * s + k;
+    if (ydir)
+      cx.store_band(s & 1, spos, gpos, band_index(g, b, end, s, k, p));
+    else
+      cx.store_band(s & 1, gpos, spos, band_index(g, b, end, s, k, p));
+  });
+  if (write_top) {
+    const int g0 = half + R - R * hh, gw = 2 * R * hh, s0 = R + R * hh, sw = W - 2 * R * hh;
+    if (sw > 0)
+      cx.for_grid(ydir ? gw : sw, ydir ? sw : gw, [&](int b2, int a) {
+        const int lx = ydir ? s0 + a : g0 + a;
+        const int ly = ydir ? g0 + b2 : s0 + b2;
+        cx.store_u(hh & 1, lx, ly, ox + lx, oy + ly);
+      });
+  }
+}
+
+// Octahedron producing tile (tx, ty) of the tiling with offset odd * W/2: its
+// centre is a corner of the previous tiling.  The corner patches of the four
+// pyramids around it and the end bands of the four bridges meeting there are
+// inserted, the square around the corner grown for levels 1..hh, then
+//   M2_FULL: shrunk as the new tile's pyramid (levels 1..h-1 past h) and its
+//            strips exported;
+//   M2_DOWN: the completed tile (level h) written back;
+//   M2_GAP:  the grown square of level hh written back (remainder).
+template <class Cx>
+SW_HD void run_octa(Cx& cx, const Geom2& g, int64_t tx, int64_t ty, int odd, int mode, int hh) {
+  const int R = g.R, W = g.W, half = W / 2, lc = half + R;
+  const int64_t X0 = odd * half + tx * W, Y0 = odd * half + ty * W;
+  const int64_t ox = X0 - R, oy = Y0 - R;
+  // previous tiling: tiles left/right of the corner (x) and below/above it (y)
+  const int64_t lx_t = odd ? tx : tx - 1, rx_t = odd ? tx + 1 : tx;
+  const int64_t ly_t = odd ? ty : ty - 1, uy_t = odd ? ty + 1 : ty;
+  // bands: x-bridges above (low end) and below (high end), y-bridges right
+  // (low end) and left (high end)
+  cx.for_grid(4 * 2 * R * hh, 2 * R * hh, [&](int oo, int p) {
+    const int s = oo % hh;
+    const int rest = oo / hh;
+    const int k = rest % (2 * R);
+    const int piece = rest / (2 * R);
+    if (p >= 2 * R * s) return;
+    const int along = lc - R * s + p;
+    const int near_hi = lc + R * s + k, near_lo = lc - R * s - 2 * R + k;
+    if (piece == 0)
+      cx.load_band(s & 1, along, near_hi, band_index(g, xbridge_id(g, lx_t, uy_t), 0, s, k, p));
+    else if (piece == 1)
+      cx.load_band(s & 1, along, near_lo, band_index(g, xbridge_id(g, lx_t, ly_t), 1, s, k, p));
+    else if (piece == 2)
+      cx.load_band(s & 1, near_hi, along, band_index(g, ybridge_id(g, rx_t, ly_t), 0, s, k, p));
+    else
+      cx.load_band(s & 1, near_lo, along, band_index(g, ybridge_id(g, lx_t, ly_t), 1, s, k, p));
+  });
+  // pyramid corner patches from the left (side 0) / right (side 1) strips
+  cx.for_grid(4 * 2 * R * hh, 2 * R, [&](int oo, int p) {
+    const int s = oo % hh;
+    const int rest = oo / hh;
+    const int k = rest % (2 * R);
+    const int piece = rest / (2 * R);  // 0 upper-right, 1 upper-left, 2 lower-right, 3 lower-left
+    const bool right = piece == 0 || piece == 2, upper = piece < 2;
+    const int lx = right ? lc + R * s + k : lc - R * s - 2 * R + k;
+    const int ly = upper ? lc + R * s + p : lc - R * s - 2 * R + p;
+    const int pos = upper ? p : strip_len(g, s) - 2 * R + p;
+    const int64_t tile = tile_id(g, right ? rx_t : lx_t, upper ? uy_t : ly_t);
+    cx.load_strip(s & 1, lx, ly, strip_index(g, tile, right ? 0 : 1, s, k, pos));
+  });
+  cx.sync();
+  for (int s = 1; s <= hh; ++s) cx.level(s, 0, lc - R * s, lc + R * s, lc - R * s, lc + R * s, ox, oy);
+  if (mode == M2_FULL) {
+    for (int s = 1; s < g.h; ++s) cx.level(s, g.h, R + R * s, W + R - R * s, R + R * s, W + R - R * s, ox, oy);
+    export_strips(cx, g, tile_id(g, tx, ty), g.h);
+  } else if (mode == M2_DOWN) {
+    cx.for_grid(W, W, [&](int b, int a) { cx.store_u(g.h & 1, R + a, R + b, X0 + a, Y0 + b); });
+  } else {
+    const int lo = lc - R * hh, w = 2 * R * hh;
+    cx.for_grid(w, w, [&](int b, int a) { cx.store_u(hh & 1, lo + a, lo + b, ox + lo + a, oy + lo + b); });
+  }
+}
+
+// The launch sequence for n levels: q = n / h full half cycles (PYR, then q
+// times BRIDGE + OCTA, the last OCTA writing the state) and, for rem = n % h,
+// a PYR / BRIDGE / OCTA triple truncated at rem.
+//   emit(kind, par, mode, hh, cycle):  cycle c >= 0 of a full pass (PYR: 0;
+//   BRIDGE and OCTA of half cycle c >= 1), -1 for the remainder.  par is the
+//   tiling parity of PYR / BRIDGE (offset par * W/2) and of the tiling an
+//   OCTA produces.  Strips: PYR and OCTA of cycle c write buffer c & 1;
+//   BRIDGE and OCTA of cycle c read buffer (c - 1) & 1; the remainder uses
+//   buffer 0.
+template <class F>
+inline void for_each_launch2d(const Geom2& g, int64_t n, F emit) {
+  const int64_t q = n / g.h;
+  const int rem = (int)(n % g.h);
+  if (q > 0) {
+    emit(K_PYR, 0, M2_FULL, g.h, (int64_t)0);
+    for (int64_t c = 1; c <= q; ++c) {
+      emit(K_BRIDGE, (int)((c - 1) & 1), M2_FULL, g.h, c);
+      emit(K_OCTA, (int)(c & 1), c == q ? M2_DOWN : M2_FULL, g.h, c);
+    }
+  }
+  if (rem > 0) {
+    emit(K_PYR, 0, M2_GAP, rem, (int64_t)-1);
+    emit(K_BRIDGE, 0, M2_GAP, rem, (int64_t)-1);
+    emit(K_OCTA, 1, M2_GAP, rem, (int64_t)-1);
+  }
+}
+
+inline int64_t launch_count2d(const Geom2& g, int64_t n) {
+  const int64_t q = n / g.h;
+  return (q > 0 ? 1 + 2 * q : 0) + (n % g.h ? 3 : 0);
+}
+
+}  // namespace swept2d

@@ -394,3 +394,118 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# --------------------------------------------------------------------------- 2D (include/swept2d.h)
+class swept2d_config(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("bc", ctypes.c_int32), ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+                ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("tile_w", ctypes.c_int32), ("threads", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+class swept2d_plan_info(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int32), ("threads", ctypes.c_int32), ("half_cycle", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("tiles_x", ctypes.c_int64), ("tiles_y", ctypes.c_int64),
+                ("smem_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64)]
+
+
+swept2d_init = _sig("swept2d_init", [ctypes.POINTER(swept2d_config), ctypes.POINTER(_H)])
+swept2d_workspace_size = _sig("swept2d_workspace_size", [_H, ctypes.POINTER(_SZ)])
+swept2d_bind_workspace = _sig("swept2d_bind_workspace", [_H, _P, _SZ])
+swept2d_step_n = _sig("swept2d_step_n", [_H, _P, _I64, _P])
+classic2d_step_n = _sig("classic2d_step_n", [_H, _P, _I64, _P])
+swept2d_get_plan = _sig("swept2d_get_plan", [_H, ctypes.POINTER(swept2d_plan_info)])
+swept2d_check_schedule = _sig("swept2d_check_schedule", [_H, _I64, ctypes.POINTER(_I64)])
+swept2d_last_error = _sig("swept2d_last_error", [_H, ctypes.c_char_p, _SZ])
+swept2d_free = _sig("swept2d_free", [_H], None)
+
+
+def make_config2d(dtype, nx, ny, dx, dt, alpha, tile_w=0, threads=0, bc=BC_PERIODIC):
+    c = swept2d_config()
+    c.dtype, c.bc, c.nx, c.ny = int(dtype), int(bc), int(nx), int(ny)
+    c.dx, c.dt, c.alpha = float(dx), float(dt), float(alpha)
+    c.tile_w, c.threads = int(tile_w), int(threads)
+    return c
+
+
+def _err2d(h):
+    buf = ctypes.create_string_buffer(512)
+    swept2d_last_error(h, buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+class Solver2D:
+    """A 2D swept handle plus its workspace (a torch uint8 tensor on the current
+    device).  States are contiguous CUDA tensors of shape (ny, nx)."""
+
+    def __init__(self, dtype, nx, ny, dx, dt, alpha, tile_w=0, threads=0):
+        import torch
+
+        self.cfg = make_config2d(dtype, nx, ny, dx, dt, alpha, tile_w, threads)
+        h = _H()
+        st = swept2d_init(ctypes.byref(self.cfg), ctypes.byref(h))
+        if st != SWEPT_OK:
+            raise SweptError(st, "swept2d_init rejected the configuration")
+        self.h = h.value
+        self.nx, self.ny = nx, ny
+        self.torch_dtype = torch.float32 if dtype == F32 else torch.float64
+        sz = _SZ()
+        self._check(swept2d_workspace_size(self.h, ctypes.byref(sz)), "swept2d_workspace_size")
+        self.ws = torch.empty(int(sz.value), dtype=torch.uint8, device="cuda")
+        self._check(swept2d_bind_workspace(self.h, ctypes.c_void_p(self.ws.data_ptr()), sz.value),
+                    "swept2d_bind_workspace")
+        p = swept2d_plan_info()
+        self._check(swept2d_get_plan(self.h, ctypes.byref(p)), "swept2d_get_plan")
+        self.plan = {f: getattr(p, f) for f, _ in p._fields_}
+
+    def _check(self, st, what):
+        if st != SWEPT_OK:
+            raise SweptError(st, what + ": " + _err2d(self.h))
+
+    def _check_u(self, u):
+        if not u.is_cuda or not u.is_contiguous() or u.dtype != self.torch_dtype or u.numel() != self.nx * self.ny:
+            raise ValueError("u must be a contiguous CUDA tensor of %d values of dtype %s"
+                             % (self.nx * self.ny, self.torch_dtype))
+
+    def step(self, u, nsteps, stream=None):
+        """swept2d_step_n on u in place (asynchronous on the stream)."""
+        self._check_u(u)
+        self._check(swept2d_step_n(self.h, ctypes.c_void_p(u.data_ptr()), int(nsteps), _stream_ptr(stream)),
+                    "swept2d_step_n")
+        return u
+
+    def classic(self, u, nsteps, stream=None):
+        """classic2d_step_n on u in place (asynchronous on the stream)."""
+        self._check_u(u)
+        self._check(classic2d_step_n(self.h, ctypes.c_void_p(u.data_ptr()), int(nsteps), _stream_ptr(stream)),
+                    "classic2d_step_n")
+        return u
+
+    def close(self):
+        if self.h:
+            swept2d_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def check_schedule2d(dtype, nx, ny, tile_w, nsteps, threads=0):
+    """Host-only symbolic replay of the 2D launch sequence (no GPU): returns the
+    number of point updates, raises SweptError with the first violation."""
+    cfg = make_config2d(dtype, nx, ny, 1.0, 0.2, 1.0, tile_w, threads)
+    h = _H()
+    st = swept2d_init(ctypes.byref(cfg), ctypes.byref(h))
+    if st != SWEPT_OK:
+        raise SweptError(st, "swept2d_init rejected the configuration")
+    try:
+        n = _I64()
+        st = swept2d_check_schedule(h.value, int(nsteps), ctypes.byref(n))
+        if st != SWEPT_OK:
+            raise SweptError(st, _err2d(h.value))
+        return n.value
+    finally:
+        swept2d_free(h.value)
