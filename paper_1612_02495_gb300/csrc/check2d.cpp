@@ -68,6 +68,7 @@ struct Sim2 {
 };
 
 struct Host2Ctx {
+  static constexpr int kR = 0;  // radius from the geometry
   Sim2& sim;
   const Geom2& g;
   int64_t block;
@@ -84,6 +85,15 @@ struct Host2Ctx {
       for (int i = 0; i < nin; ++i) f(o, i);
   }
   void sync() {}
+  void divmod(int a, int b, int& q, int& r) const {
+    if (a < 0 || a > 1024 || b < 1 || b > 256) sim.fail("divmod operands outside the device's exact range");
+    q = a / b;
+    r = a % b;
+  }
+  int64_t wrap_once(int64_t x, int64_t n) const {
+    if (x < -n || x >= 2 * n) sim.fail("window more than one period outside the grid");
+    return wrap_n(x, n);
+  }
   Tag& cell(int r, int lx, int ly) {
     if (lx < 0 || lx >= g.M || ly < 0 || ly >= g.M) {
       sim.fail("window index out of range");
@@ -92,7 +102,7 @@ struct Host2Ctx {
     }
     return w[((size_t)r * g.M + ly) * g.M + lx];
   }
-  int64_t gp(int64_t gx, int64_t gy) const { return wrap_n(gy, g.ny) * g.nx + wrap_n(gx, g.nx); }
+  int64_t gp(int64_t gx, int64_t gy) const { return wrap_once(gy, g.ny) * g.nx + wrap_once(gx, g.nx); }
   void load_u(int r, int lx, int ly, int64_t gx, int64_t gy) {
     const size_t i = (size_t)gp(gx, gy);
     sim.note(sim.au, i, block, false, "u");

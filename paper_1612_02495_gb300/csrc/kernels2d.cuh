@@ -28,11 +28,22 @@ __device__ __forceinline__ T heat2d_point(const T* c, int M, const Heat2dK<T>& k
   return fma_rn(k.fo, add_rn(sx, sy), mul_rn(k.c1, c[0]));
 }
 
+// q = a / b, r = a - q b for 0 <= a <= 1024, 1 <= b <= 256, through one
+// single-precision multiply: with rb the correctly rounded 1/b, (a + 1/2) rb
+// is within 2^-10 of (a + 1/2) / b, which is at least 1/(2b) >= 2^-9 away from
+// an integer, so truncation gives the exact quotient (checked exhaustively
+// over that range).
+__device__ __forceinline__ void divmod_small(int a, int b, int& q, int& r) {
+  q = (int)(((float)a + 0.5f) * __frcp_rn((float)b));
+  r = a - q * b;
+}
+
 // Device context of one block: the two level rows of its (W + 2R)^2 window in
-// shared memory; rows of the window are spread over warps, points of a row
-// over lanes.
+// shared memory.  Loads and stores spread rows over warps and points of a row
+// over lanes; a level spreads its rectangle flat over the block.
 template <typename T>
 struct Dev2Ctx {
+  static constexpr int kR = 1;  // the 5-point heat stencil
   T* sm;
   Geom2 g;
   Heat2dK<T> k;
@@ -43,8 +54,10 @@ struct Dev2Ctx {
   T* b_out;
 
   __device__ __forceinline__ T& at(int r, int lx, int ly) { return sm[((int64_t)r * g.M + ly) * g.M + lx]; }
+  // a window lies within one period of the grid: -R <= coordinate < n + W + R
+  __device__ __forceinline__ static int64_t wrap1(int64_t x, int64_t n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
   __device__ __forceinline__ int64_t gidx(int64_t gx, int64_t gy) const {
-    return wrap_n(gy, g.ny) * g.nx + wrap_n(gx, g.nx);
+    return wrap1(gy, g.ny) * g.nx + wrap1(gx, g.nx);
   }
   template <class F>
   __device__ __forceinline__ void for_grid(int nout, int nin, F&& f) {
@@ -53,6 +66,8 @@ struct Dev2Ctx {
       for (int i = lane; i < nin; i += 32) f(o, i);
   }
   __device__ __forceinline__ void sync() { __syncthreads(); }
+  // the loop indices the phases split are < 1024 and the divisors <= 64
+  __device__ __forceinline__ void divmod(int a, int b, int& q, int& r) const { divmod_small(a, b, q, r); }
   __device__ __forceinline__ void load_u(int r, int lx, int ly, int64_t gx, int64_t gy) {
     at(r, lx, ly) = u[gidx(gx, gy)];
   }
@@ -63,14 +78,34 @@ struct Dev2Ctx {
   __device__ __forceinline__ void store_strip(int r, int lx, int ly, int64_t e) { s_out[e] = at(r, lx, ly); }
   __device__ __forceinline__ void load_band(int r, int lx, int ly, int64_t e) { at(r, lx, ly) = b_in[e]; }
   __device__ __forceinline__ void store_band(int r, int lx, int ly, int64_t e) { b_out[e] = at(r, lx, ly); }
-  // level s on the local rectangle [x0, x1) x [y0, y1): row s & 1 from row (s - 1) & 1
+  // level s on the local rectangle [x0, x1) x [y0, y1): row s & 1 from row
+  // (s - 1) & 1.  The rectangle's points are spread flat over the block (point
+  // i = y w + x to thread i mod blockDim), so narrow regions (bridges, small
+  // corners) still fill whole warps.
   __device__ __forceinline__ void level(int s, int, int x0, int x1, int y0, int y1, int64_t, int64_t) {
     const int M = g.M;
     const T* in = sm + (int64_t)((s & 1) ^ 1) * M * M;
     T* out = sm + (int64_t)(s & 1) * M * M;
-    const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31u), nw = (int)(blockDim.x >> 5);
-    for (int ly = y0 + warp; ly < y1; ly += nw)
-      for (int lx = x0 + lane; lx < x1; lx += 32) out[ly * M + lx] = heat2d_point<T>(in + ly * M + lx, M, k);
+    const int w = x1 - x0, n = w * (y1 - y0);
+    const int t = (int)threadIdx.x, nt = (int)blockDim.x;
+    if (t < n) {
+      int y, x, dy, dx;
+      divmod_small(t, w, y, x);
+      divmod_small(nt, w, dy, dx);
+      T* o = out + (y0 + y) * M + x0;
+      const T* c = in + (y0 + y) * M + x0;
+      for (int i = t; i < n; i += nt) {
+        o[x] = heat2d_point<T>(c + x, M, k);
+        x += dx;
+        o += dy * M;
+        c += dy * M;
+        if (x >= w) {
+          x -= w;
+          o += M;
+          c += M;
+        }
+      }
+    }
     __syncthreads();
   }
 };

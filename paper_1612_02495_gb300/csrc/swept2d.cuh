@@ -59,28 +59,46 @@ struct Geom2 {
 
 SW_HD int strip_len(const Geom2& g, int s) { return g.W - 2 * g.R * s; }
 SW_HD int64_t strip_off(const Geom2& g, int s) { return (int64_t)s * g.W - (int64_t)g.R * s * (s - 1); }
+// offset of (side, s, k, p) inside one tile's strip block (< Es, fits 32 bits)
+SW_HD int strip_in_tile(const Geom2& g, int side, int s, int k, int p) {
+  return side * (2 * g.R) * (int)g.Ph + 2 * g.R * (s * g.W - g.R * s * (s - 1)) + k * strip_len(g, s) + p;
+}
 SW_HD int64_t strip_index(const Geom2& g, int64_t tile, int side, int s, int k, int p) {
-  return tile * g.Es + (int64_t)side * (2 * g.R) * g.Ph + (int64_t)(2 * g.R) * strip_off(g, s) +
-         (int64_t)k * strip_len(g, s) + p;
+  return tile * g.Es + strip_in_tile(g, side, s, k, p);
 }
 SW_HD int64_t band_off(const Geom2& g, int s) { return (int64_t)g.R * s * (s - 1); }
+// offset of (end, s, k, p) inside one bridge's band block (< Eb)
+SW_HD int band_in_bridge(const Geom2& g, int end, int s, int k, int p) {
+  return end * (2 * g.R) * (int)g.Bh + 2 * g.R * (g.R * s * (s - 1)) + k * (2 * g.R * s) + p;
+}
 SW_HD int64_t band_index(const Geom2& g, int64_t bridge, int end, int s, int k, int p) {
-  return bridge * g.Eb + (int64_t)end * (2 * g.R) * g.Bh + (int64_t)(2 * g.R) * band_off(g, s) +
-         (int64_t)k * (2 * g.R * s) + p;
+  return bridge * g.Eb + band_in_bridge(g, end, s, k, p);
 }
 SW_HD int64_t tile_id(const Geom2& g, int64_t tx, int64_t ty) { return wrap_n(ty, g.nty) * g.ntx + wrap_n(tx, g.ntx); }
 // x-bridge between tiles (tx, ty) and (tx+1, ty); y-bridge between (tx, ty) and (tx, ty+1)
 SW_HD int64_t xbridge_id(const Geom2& g, int64_t tx, int64_t ty) { return tile_id(g, tx, ty); }
 SW_HD int64_t ybridge_id(const Geom2& g, int64_t tx, int64_t ty) { return g.ntx * g.nty + tile_id(g, tx, ty); }
 
+// The geometry with the radius the context fixes at compile time (Cx::kR; 0
+// keeps the runtime field, as the host checker does), so that on the device
+// the index arithmetic of the phases folds to constants.
+template <class Cx>
+SW_HD Geom2 fixed_geom2(const Geom2& g) {
+  Geom2 f = g;
+  if (Cx::kR > 0) f.R = Cx::kR;
+  return f;
+}
+
 // Export the four side strips of levels 0..hh-1 of the pyramid whose tile sits
 // at local [R, W + R)^2 (level s in row s & 1 on [R + Rs, W + R - Rs)^2).
 template <class Cx>
-SW_HD void export_strips(Cx& cx, const Geom2& g, int64_t tile, int hh) {
+SW_HD void export_strips(Cx& cx, const Geom2& g_in, int64_t tile, int hh) {
+  const Geom2 g = fixed_geom2<Cx>(g_in);
   const int R = g.R, W = g.W;
+  const int64_t base = tile * g.Es;
   cx.for_grid(4 * 2 * R * hh, W, [&](int o, int p) {
-    const int s = o % hh;
-    const int rest = o / hh;
+    int rest, s;
+    cx.divmod(o, hh, rest, s);
     const int k = rest % (2 * R);
     const int side = rest / (2 * R);
     if (p >= strip_len(g, s)) return;
@@ -88,14 +106,15 @@ SW_HD void export_strips(Cx& cx, const Geom2& g, int64_t tile, int hh) {
     const int along = R + R * s + p;
     const int lx = side < 2 ? across : along;
     const int ly = side < 2 ? along : across;
-    cx.store_strip(s & 1, lx, ly, strip_index(g, tile, side, s, k, p));
+    cx.store_strip(s & 1, lx, ly, base + strip_in_tile(g, side, s, k, p));
   });
 }
 
 // Pyramid of tile (tx, ty) of the tiling with offset par * W/2: levels 1..hh,
 // strips of levels 0..hh-1; with write_top, level hh written back (remainder).
 template <class Cx>
-SW_HD void run_pyr(Cx& cx, const Geom2& g, int64_t tx, int64_t ty, int par, int hh, bool write_top) {
+SW_HD void run_pyr(Cx& cx, const Geom2& g_in, int64_t tx, int64_t ty, int par, int hh, bool write_top) {
+  const Geom2 g = fixed_geom2<Cx>(g_in);
   const int R = g.R, W = g.W;
   const int64_t X0 = par * (W / 2) + tx * W, Y0 = par * (W / 2) + ty * W;
   const int64_t ox = X0 - R, oy = Y0 - R;
@@ -114,7 +133,8 @@ SW_HD void run_pyr(Cx& cx, const Geom2& g, int64_t tx, int64_t ty, int par, int 
 // across the boundary and shrunk along it, end bands of levels 0..hh-1
 // exported; with write_top, level hh written back (remainder).
 template <class Cx>
-SW_HD void run_bridge(Cx& cx, const Geom2& g, int64_t bid, int par, int hh, bool write_top) {
+SW_HD void run_bridge(Cx& cx, const Geom2& g_in, int64_t bid, int par, int hh, bool write_top) {
+  const Geom2 g = fixed_geom2<Cx>(g_in);
   const int R = g.R, W = g.W, half = W / 2;
   const bool ydir = bid >= g.ntx * g.nty;
   const int64_t t = ydir ? bid - g.ntx * g.nty : bid;
@@ -123,19 +143,19 @@ SW_HD void run_bridge(Cx& cx, const Geom2& g, int64_t bid, int par, int hh, bool
   // window origin; local (u, v) = (grow-axis, shrink-axis) coordinates
   const int64_t ox = ydir ? o + tx * W - R : o + (tx + 1) * W - half - R;
   const int64_t oy = ydir ? o + (ty + 1) * W - half - R : o + ty * W - R;
-  const int64_t lo_tile = tile_id(g, tx, ty);
-  const int64_t hi_tile = ydir ? tile_id(g, tx, ty + 1) : tile_id(g, tx + 1, ty);
+  const int64_t lo_base = tile_id(g, tx, ty) * g.Es;
+  const int64_t hi_base = (ydir ? tile_id(g, tx, ty + 1) : tile_id(g, tx + 1, ty)) * g.Es;
   // strips: the low tile's high side (1 right / 3 top), the high tile's low side (0 / 2)
   cx.for_grid(2 * 2 * R * hh, W, [&](int oo, int p) {
-    const int s = oo % hh;
-    const int rest = oo / hh;
+    int rest, s;
+    cx.divmod(oo, hh, rest, s);
     const int k = rest % (2 * R);
     const int which = rest / (2 * R);
     if (p >= strip_len(g, s)) return;
     const int gpos = which == 0 ? half - R - R * s + k : half + R + R * s + k;  // grow axis
     const int spos = R + R * s + p;                                             // shrink axis
     const int side = which == 0 ? (ydir ? 3 : 1) : (ydir ? 2 : 0);
-    const int64_t e = strip_index(g, which == 0 ? lo_tile : hi_tile, side, s, k, p);
+    const int64_t e = (which == 0 ? lo_base : hi_base) + strip_in_tile(g, side, s, k, p);
     if (ydir)
       cx.load_strip(s & 1, spos, gpos, e);
     else
@@ -149,19 +169,20 @@ SW_HD void run_bridge(Cx& cx, const Geom2& g, int64_t bid, int par, int hh, bool
     else
       cx.level(s, 0, g0, g1, s0, s1, ox, oy);
   }
-  const int64_t b = ydir ? ybridge_id(g, tx, ty) : xbridge_id(g, tx, ty);
+  const int64_t bbase = (ydir ? ybridge_id(g, tx, ty) : xbridge_id(g, tx, ty)) * g.Eb;
   cx.for_grid(2 * 2 * R * hh, 2 * R * hh, [&](int oo, int p) {
-    const int s = oo % hh;
-    const int rest = oo / hh;
+    int rest, s;
+    cx.divmod(oo, hh, rest, s);
     const int k = rest % (2 * R);
     const int end = rest / (2 * R);
     if (p >= 2 * R * s) return;
     const int gpos = half + R - R * s + p;
     const int spos = end == 0 ? R + R * s + k : W - R - R * s + k;
+    const int64_t e = bbase + band_in_bridge(g, end, s, k, p);
     if (ydir)
-      cx.store_band(s & 1, spos, gpos, band_index(g, b, end, s, k, p));
+      cx.store_band(s & 1, spos, gpos, e);
     else
-      cx.store_band(s & 1, gpos, spos, band_index(g, b, end, s, k, p));
+      cx.store_band(s & 1, gpos, spos, e);
   });
   if (write_top) {
     const int g0 = half + R - R * hh, gw = 2 * R * hh, s0 = R + R * hh, sw = W - 2 * R * hh;
@@ -183,44 +204,50 @@ SW_HD void run_bridge(Cx& cx, const Geom2& g, int64_t bid, int par, int hh, bool
 //   M2_DOWN: the completed tile (level h) written back;
 //   M2_GAP:  the grown square of level hh written back (remainder).
 template <class Cx>
-SW_HD void run_octa(Cx& cx, const Geom2& g, int64_t tx, int64_t ty, int odd, int mode, int hh) {
+SW_HD void run_octa(Cx& cx, const Geom2& g_in, int64_t tx, int64_t ty, int odd, int mode, int hh) {
+  const Geom2 g = fixed_geom2<Cx>(g_in);
   const int R = g.R, W = g.W, half = W / 2, lc = half + R;
   const int64_t X0 = odd * half + tx * W, Y0 = odd * half + ty * W;
   const int64_t ox = X0 - R, oy = Y0 - R;
   // previous tiling: tiles left/right of the corner (x) and below/above it (y)
   const int64_t lx_t = odd ? tx : tx - 1, rx_t = odd ? tx + 1 : tx;
   const int64_t ly_t = odd ? ty : ty - 1, uy_t = odd ? ty + 1 : ty;
+  // the four bridges meeting at the corner and the four tiles around it
+  const int64_t xb_up = xbridge_id(g, lx_t, uy_t) * g.Eb, xb_dn = xbridge_id(g, lx_t, ly_t) * g.Eb;
+  const int64_t yb_r = ybridge_id(g, rx_t, ly_t) * g.Eb, yb_l = ybridge_id(g, lx_t, ly_t) * g.Eb;
+  const int64_t t_ur = tile_id(g, rx_t, uy_t) * g.Es, t_ul = tile_id(g, lx_t, uy_t) * g.Es;
+  const int64_t t_lr = tile_id(g, rx_t, ly_t) * g.Es, t_ll = tile_id(g, lx_t, ly_t) * g.Es;
   // bands: x-bridges above (low end) and below (high end), y-bridges right
   // (low end) and left (high end)
   cx.for_grid(4 * 2 * R * hh, 2 * R * hh, [&](int oo, int p) {
-    const int s = oo % hh;
-    const int rest = oo / hh;
+    int rest, s;
+    cx.divmod(oo, hh, rest, s);
     const int k = rest % (2 * R);
     const int piece = rest / (2 * R);
     if (p >= 2 * R * s) return;
     const int along = lc - R * s + p;
     const int near_hi = lc + R * s + k, near_lo = lc - R * s - 2 * R + k;
     if (piece == 0)
-      cx.load_band(s & 1, along, near_hi, band_index(g, xbridge_id(g, lx_t, uy_t), 0, s, k, p));
+      cx.load_band(s & 1, along, near_hi, xb_up + band_in_bridge(g, 0, s, k, p));
     else if (piece == 1)
-      cx.load_band(s & 1, along, near_lo, band_index(g, xbridge_id(g, lx_t, ly_t), 1, s, k, p));
+      cx.load_band(s & 1, along, near_lo, xb_dn + band_in_bridge(g, 1, s, k, p));
     else if (piece == 2)
-      cx.load_band(s & 1, near_hi, along, band_index(g, ybridge_id(g, rx_t, ly_t), 0, s, k, p));
+      cx.load_band(s & 1, near_hi, along, yb_r + band_in_bridge(g, 0, s, k, p));
     else
-      cx.load_band(s & 1, near_lo, along, band_index(g, ybridge_id(g, lx_t, ly_t), 1, s, k, p));
+      cx.load_band(s & 1, near_lo, along, yb_l + band_in_bridge(g, 1, s, k, p));
   });
   // pyramid corner patches from the left (side 0) / right (side 1) strips
   cx.for_grid(4 * 2 * R * hh, 2 * R, [&](int oo, int p) {
-    const int s = oo % hh;
-    const int rest = oo / hh;
+    int rest, s;
+    cx.divmod(oo, hh, rest, s);
     const int k = rest % (2 * R);
     const int piece = rest / (2 * R);  // 0 upper-right, 1 upper-left, 2 lower-right, 3 lower-left
     const bool right = piece == 0 || piece == 2, upper = piece < 2;
     const int lx = right ? lc + R * s + k : lc - R * s - 2 * R + k;
     const int ly = upper ? lc + R * s + p : lc - R * s - 2 * R + p;
     const int pos = upper ? p : strip_len(g, s) - 2 * R + p;
-    const int64_t tile = tile_id(g, right ? rx_t : lx_t, upper ? uy_t : ly_t);
-    cx.load_strip(s & 1, lx, ly, strip_index(g, tile, right ? 0 : 1, s, k, pos));
+    const int64_t base = piece == 0 ? t_ur : (piece == 1 ? t_ul : (piece == 2 ? t_lr : t_ll));
+    cx.load_strip(s & 1, lx, ly, base + strip_in_tile(g, right ? 0 : 1, s, k, pos));
   });
   cx.sync();
   for (int s = 1; s <= hh; ++s) cx.level(s, 0, lc - R * s, lc + R * s, lc - R * s, lc + R * s, ox, oy);

@@ -125,3 +125,14 @@ def test_swept2d_repeated_calls_and_zero_steps(S):
     ref = oracle.heat2d(p["u0"], p["dx"], p["dt"], p["alpha"], 75)
     assert np.array_equal(u.cpu().numpy(), ref)
     sol.close()
+
+
+def test_small_divmod_argument_is_exact():
+    """The 2D level mapping divides thread indices (<= 1024) by rectangle widths
+    (<= 256) with one single-precision multiply by the correctly rounded
+    reciprocal; check that argument exhaustively in IEEE single precision."""
+    a = np.arange(0, 1025, dtype=np.int64)
+    for b in range(1, 257):
+        rb = np.float32(1.0) / np.float32(b)
+        q = ((a.astype(np.float32) + np.float32(0.5)) * rb).astype(np.int64)
+        assert np.array_equal(q, a // b), b
