@@ -311,6 +311,48 @@ def measure_sizes(S, autotune, torch, stream, barrier, ws, flush):
     return out
 
 
+# the 2D swept decomposition (the paper's future work): 2D FTCS heat, periodic
+HEAT2D_CASES = [
+    ("heat2d 1024x1024 FP64, 1,000 steps", "f64", 1024, 1000),
+    ("heat2d 1024x1024 FP32, 1,000 steps", "f32", 1024, 1000),
+    ("heat2d 4096x4096 FP32, 100 steps", "f32", 4096, 100),
+]
+
+
+def measure_heat2d(S, autotune, torch, stream, barrier, ws, flush):
+    """Each HEAT2D_CASES workload with its autotuned 2D swept plan and with the
+    classic 2D path (CUDA events on the launching stream, L2 flushed before each
+    timed solve, best of three)."""
+    from paper_1612_02495_gb300 import inputs
+
+    out = []
+    for label, dt, n, nsteps in HEAT2D_CASES:
+        code = S.F64 if dt == "f64" else S.F32
+        plan = autotune.tune_2d(code, n, n, probe_steps=min(nsteps, 200))
+        p = inputs.heat2d_problem(nx=n, ny=n, dtype=np.float64 if dt == "f64" else np.float32)
+        sol = S.Solver2D(code, n, n, p["dx"], p["dt"], p["alpha"], tile_w=plan["tile_w"], threads=plan["threads"])
+        d0 = torch.from_numpy(p["u0"]).cuda()
+        u = d0.clone()
+        res = {}
+        for name, fn in (("swept", sol.step), ("classic", sol.classic)):
+            fn(u, nsteps)
+            best = None
+            for _ in range(3):
+                u.copy_(d0)
+                flush.zero_()
+                ev = _event_time(torch, stream, lambda: fn(u, nsteps))
+                barrier()
+                t = ev[0].elapsed_time(ev[1])
+                best = t if best is None else min(best, t)
+            res[name] = best
+        sol.close()
+        out.append({"workload": label, "swept_ms": res["swept"], "classic_ms": res["classic"],
+                    "speedup_vs_classic": res["classic"] / res["swept"],
+                    "swept_value": ws * n * n * nsteps / (res["swept"] * 1e-3), "unit": UNIT,
+                    "plan": {"tile_w": plan["tile_w"], "threads": plan["threads"]}})
+    return out
+
+
 def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
@@ -353,6 +395,7 @@ def main():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-sizes", action="store_true")
+    ap.add_argument("--no-2d", action="store_true")
     ap.add_argument("--batch-f64", action="store_true", help="also time the FP64 batch (about 50 s)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -479,6 +522,9 @@ def main():
     sizes = None
     if not args.no_sizes:
         sizes = measure_sizes(S, autotune, torch, stream, barrier, ws, flush)
+    heat2d = None
+    if not args.no_2d:
+        heat2d = measure_heat2d(S, autotune, torch, stream, barrier, ws, flush)
     batched = None
     if not args.no_batch:
         batched = measure_batch(S, inputs, autotune, torch, stream, barrier, ws, args.batch_f64)
@@ -501,6 +547,8 @@ def main():
         out["batched"] = batched
     if sizes:
         out["sizes"] = sizes
+    if heat2d:
+        out["heat2d"] = heat2d
     out["config"]["autotuned"] = {k: tuned.get(k, 0) for k in ("tile_w", "threads", "warp_tiles", "persistent",
                                                                 "cluster")}
     if ms_classic:
