@@ -28,15 +28,17 @@ __device__ __forceinline__ T heat2d_point(const T* c, int M, const Heat2dK<T>& k
   return fma_rn(k.fo, add_rn(sx, sy), mul_rn(k.c1, c[0]));
 }
 
-// q = a / b, r = a - q b for 0 <= a <= 1024, 1 <= b <= 256, through one
-// single-precision multiply: with rb the correctly rounded 1/b, (a + 1/2) rb
-// is within 2^-10 of (a + 1/2) / b, which is at least 1/(2b) >= 2^-9 away from
-// an integer, so truncation gives the exact quotient (checked exhaustively
-// over that range).
-__device__ __forceinline__ void divmod_small(int a, int b, int& q, int& r) {
-  q = (int)(((float)a + 0.5f) * __frcp_rn((float)b));
+// q = a / b, r = a - q b for 0 <= a <= 1024, 1 <= b <= 256, from rb, an
+// approximation of 1/b in single precision.  (a + 1/2) / b lies at least
+// 1/(2b) >= 2^-9 away from an integer, and (a + 1/2) * rb is within a few
+// ulp of it (at most 2^-11 absolute for quotients below 1025) when rb is
+// within 2 ulp of 1/b, so truncation gives the exact quotient.
+__device__ __forceinline__ float recip_small(int b) { return __fdividef(1.0f, (float)b); }
+__device__ __forceinline__ void divmod_small(int a, int b, float rb, int& q, int& r) {
+  q = (int)(((float)a + 0.5f) * rb);
   r = a - q * b;
 }
+__device__ __forceinline__ void divmod_small(int a, int b, int& q, int& r) { divmod_small(a, b, recip_small(b), q, r); }
 
 // Device context of one block: the two level rows of its (W + 2R)^2 window in
 // shared memory.  Loads and stores spread rows over warps and points of a row
@@ -90,8 +92,9 @@ struct Dev2Ctx {
     const int t = (int)threadIdx.x, nt = (int)blockDim.x;
     if (t < n) {
       int y, x, dy, dx;
-      divmod_small(t, w, y, x);
-      divmod_small(nt, w, dy, dx);
+      const float rw = recip_small(w);
+      divmod_small(t, w, rw, y, x);
+      divmod_small(nt, w, rw, dy, dx);
       T* o = out + (y0 + y) * M + x0;
       const T* c = in + (y0 + y) * M + x0;
       for (int i = t; i < n; i += nt) {

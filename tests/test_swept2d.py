@@ -129,10 +129,17 @@ def test_swept2d_repeated_calls_and_zero_steps(S):
 
 def test_small_divmod_argument_is_exact():
     """The 2D level mapping divides thread indices (<= 1024) by rectangle widths
-    (<= 256) with one single-precision multiply by the correctly rounded
-    reciprocal; check that argument exhaustively in IEEE single precision."""
-    a = np.arange(0, 1025, dtype=np.int64)
+    (<= 256) with one single-precision multiply by an approximate reciprocal
+    (within 2 ulp of 1/b).  The quotient (a + 1/2) / b stays at least 1/(2b)
+    from an integer; check that this margin exceeds the worst error of the
+    product (3 ulp of 1/b carried through, plus the product's rounding) over the
+    whole range, and that truncation is exact with the rounded reciprocal."""
+    a = np.arange(0, 1025, dtype=np.float64)
     for b in range(1, 257):
+        exact = (a + 0.5) / b
+        margin = np.min(np.abs(exact - np.round(exact)))
+        worst = exact.max() * (3 * 2.0 ** -23) + 2.0 ** -13  # reciprocal error + product rounding
+        assert margin > worst, b
         rb = np.float32(1.0) / np.float32(b)
         q = ((a.astype(np.float32) + np.float32(0.5)) * rb).astype(np.int64)
-        assert np.array_equal(q, a // b), b
+        assert np.array_equal(q, np.arange(0, 1025) // b), b
