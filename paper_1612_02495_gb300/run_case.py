@@ -1,6 +1,6 @@
 """Run one solve of a configuration through the C ABI and print its time.
 
-  python -m paper_1612_02495_gb300.run_case --scheme ks --dtype f64 --n 1048576 \\
+  python -m paper_1612_02495_gb300.run_case --scheme ks|heat|euler|heat2d --dtype f64 --n 1048576 \\
       --nsteps 600 [--path swept|classic] [--tile 0] [--threads 0] [--chunk 0] [--persistent 0] [--cluster 0] [--warp-tiles 0] [--repeat 1]
 
 Used to profile a single kernel on a chosen size (e.g. under ncu).  One
@@ -15,7 +15,7 @@ import numpy as np
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--scheme", default="ks", choices=["heat", "ks", "euler"])
+    ap.add_argument("--scheme", default="ks", choices=["heat", "ks", "euler", "heat2d"])
     ap.add_argument("--dtype", default="f64", choices=["f32", "f64"])
     ap.add_argument("--n", type=int, default=1 << 20)
     ap.add_argument("--nsteps", type=int, default=600)
@@ -36,6 +36,8 @@ def main(argv=None):
 
     npd = np.float64 if a.dtype == "f64" else np.float32
     dt_code = S.F64 if a.dtype == "f64" else S.F32
+    if a.scheme == "heat2d":
+        return run_heat2d(a, S, inputs, torch, npd, dt_code)
     if a.scheme == "heat":
         p = inputs.heat_problem(n=a.n, dtype=npd)
         args = (S.HEAT, dt_code, a.n, p["dx"], p["dt"], p["alpha"], S.BC_PERIODIC)
@@ -69,6 +71,31 @@ def main(argv=None):
     print(json.dumps({"scheme": a.scheme, "dtype": a.dtype, "n": a.n, "nsteps": a.nsteps, "path": a.path,
                       "plan": sol.plan, "ms": ms,
                       "cell_updates_per_s": a.n * a.nsteps / (ms * 1e-3)}))
+    sol.close()
+    return 0
+
+
+def run_heat2d(a, S, inputs, torch, npd, dt_code):
+    """2D heat on an n x n grid (--n is the side): swept2d_step_n or classic2d_step_n."""
+    p = inputs.heat2d_problem(nx=a.n, ny=a.n, dtype=npd)
+    sol = S.Solver2D(dt_code, a.n, a.n, p["dx"], p["dt"], p["alpha"], tile_w=a.tile, threads=a.threads)
+    u_init = torch.from_numpy(p["u0"]).cuda()
+    u = u_init.clone()
+    run = sol.step if a.path == "swept" else sol.classic
+    run(u, a.nsteps)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(a.repeat):
+        u.copy_(u_init)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run(u, a.nsteps)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = float(np.median(times))
+    print(json.dumps({"scheme": "heat2d", "dtype": a.dtype, "n": a.n, "nsteps": a.nsteps, "path": a.path,
+                      "plan": sol.plan, "ms": ms, "cell_updates_per_s": a.n * a.n * a.nsteps / (ms * 1e-3)}))
     sol.close()
     return 0
 
