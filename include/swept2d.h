@@ -75,10 +75,10 @@ typedef struct swept2d_handle swept2d_handle;
  * SWEPT_EINVAL for an invalid configuration (*out is then NULL). */
 swept_status swept2d_init(const swept2d_config* cfg, swept2d_handle** out);
 
-/* Bytes of device workspace the handle needs: two strip buffers (4 W^2 values
- * per tile each, the pyramids' side strips of every level), one band buffer
- * (2 W^2 values per tile: the bridges' end bands), the classic path's second
- * state array and a status word. */
+/* Bytes of device workspace the handle needs: two strip buffers (2 W^2 + 4 W
+ * values per tile each: the pyramids' side strips of every level), one band
+ * buffer (2 W^2 - 4 W values per tile: the end bands of its two bridges), the
+ * classic path's second state array and a status word. */
 swept_status swept2d_workspace_size(const swept2d_handle* h, size_t* bytes);
 
 /* Bind caller-owned device memory (256-byte aligned, at least

@@ -52,8 +52,9 @@ def test_init2d_plan_and_workspace(S):
     assert p.smem_bytes == 2 * 34 * 34 * 4
     sz = ctypes.c_size_t()
     assert S.swept2d_workspace_size(h.value, ctypes.byref(sz)) == S.SWEPT_OK
-    # two strip buffers of 4 W^2 - 2W values... at least the classic second array
-    assert sz.value >= 512 * 256 * 4 * 3
+    # per tile: two strip buffers of 2 W^2 + 4 W values and bands of 2 W^2 - 4 W; plus the classic second array
+    W, tiles = 32, 16 * 8
+    assert sz.value >= 4 * (tiles * (2 * (2 * W * W + 4 * W) + (2 * W * W - 4 * W)) + 512 * 256)
     S.swept2d_free(h.value)
 
 
