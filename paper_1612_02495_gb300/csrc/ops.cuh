@@ -90,12 +90,31 @@ struct KsOp {
 //   stage 1:  t = fma(-dt/dx, F+ - F-, U1);  U' = 0.5 (U + t)
 // Across a reflective wall a cell is read as its mirror with u negated.
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T minmod(T a, T b) {
-  if (a > T(0) && b > T(0)) return a <= b ? a : b;
-  if (a < T(0) && b < T(0)) return a >= b ? a : b;
-  return T(0);
+// minmod(a, b): the argument of smaller magnitude when a and b are both
+// positive or both negative, else 0.  Evaluated on the integer pipe from the
+// IEEE bit patterns: for values of one sign, magnitude order is the order of
+// the patterns' magnitude fields, and with equal sign bits a <= b (both
+// positive) and a >= b (both negative) are both "bits(a) <= bits(b)" as signed
+// integers.  The selection equals the comparison form for every non-NaN input
+// (signed zeros, subnormals, infinities included), without spending FP64 issue
+// slots on sign tests and compares.
+__device__ __forceinline__ double minmod(double a, double b) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  const long long mag = 0x7fffffffffffffffLL;
+  const bool same_sign_nonzero = ((ia ^ ib) >= 0) && (ia & mag) != 0 && (ib & mag) != 0;
+  return same_sign_nonzero ? (ia <= ib ? a : b) : 0.0;
 }
+__device__ __forceinline__ float minmod(float a, float b) {
+  const int ia = __float_as_int(a), ib = __float_as_int(b);
+  const int mag = 0x7fffffff;
+  const bool same_sign_nonzero = ((ia ^ ib) >= 0) && (ia & mag) != 0 && (ib & mag) != 0;
+  return same_sign_nonzero ? (ia <= ib ? a : b) : 0.0f;
+}
+// the larger of two non-negative values, by their bit patterns (same rule)
+__device__ __forceinline__ double max_nonneg(double a, double b) {
+  return __double_as_longlong(a) >= __double_as_longlong(b) ? a : b;
+}
+__device__ __forceinline__ float max_nonneg(float a, float b) { return __float_as_int(a) >= __float_as_int(b) ? a : b; }
 
 template <typename T>
 struct EulerOp {
@@ -143,7 +162,8 @@ struct EulerOp {
   }
   // Rusanov flux from the two sides: 1/2 (F(L) + F(R)) - 1/2 s (U_R - U_L),
   // s = the larger of |u| + c over the two sides
-  __device__ __forceinline__ static T smax(const Side& L, const Side& R) { return L.sp >= R.sp ? L.sp : R.sp; }
+  // sp = |u| + c >= 0 on both sides
+  __device__ __forceinline__ static T smax(const Side& L, const Side& R) { return max_nonneg(L.sp, R.sp); }
   __device__ __forceinline__ static T flux0(const Side& L, const Side& R, T s) {
     return mul_rn(T(0.5), fma_rn(-s, sub_rn(R.r, L.r), add_rn(L.m, R.m)));
   }

@@ -104,6 +104,25 @@ __global__ void k_empty(float* out) {
   if (threadIdx.x == 9999) out[0] = 1.f;
 }
 
+// cycles one warp FP64 FMA holds the SMSP when only `active` lanes run it (one
+// warp alone on an SM, 4 independent chains): masked lanes may or may not be free
+__global__ void k_dfma_lanes(int active, int iters, double a, double b, double* out, long long* cyc) {
+  const int lane = threadIdx.x;
+  double x0 = lane, x1 = lane + 1, x2 = lane + 2, x3 = lane + 3;
+  const long long t0 = clock64();
+  if (lane < active)
+    for (int i = 0; i < iters; ++i) {
+      x0 = __fma_rn(x0, a, b);
+      x1 = __fma_rn(x1, a, b);
+      x2 = __fma_rn(x2, a, b);
+      x3 = __fma_rn(x3, a, b);
+    }
+  __syncwarp();
+  const long long t1 = clock64();
+  out[lane] = x0 + x1 + x2 + x3;
+  if (lane == 0) *cyc = t1 - t0;
+}
+
 int main() {
   cudaDeviceProp p;
   CK(cudaGetDeviceProperties(&p, 0));
@@ -171,7 +190,18 @@ int main() {
   cudaEventRecord(b, s);
   cudaEventSynchronize(b);
   cudaEventElapsedTime(&ms, a, b);
-  printf(", \"graph_node_us\": %.3f}\n", ms * 1e3 / 4000);
+  printf(", \"graph_node_us\": %.3f", ms * 1e3 / 4000);
+  long long* cyc;
+  CK(cudaMalloc(&cyc, sizeof(long long)));
+  for (int active : {32, 8, 1}) {
+    long long c = 0;
+    for (int rep = 0; rep < 2; ++rep) {  // the first run warms up
+      k_dfma_lanes<<<1, 32>>>(active, 4096, 0.999999, 1e-9, d, cyc);
+      CK(cudaMemcpy(&c, cyc, sizeof c, cudaMemcpyDeviceToHost));
+    }
+    printf(", \"fp64_fma_cycles_per_warp_instr_%d_lanes\": %.2f", active, (double)c / (4.0 * 4096));
+  }
+  printf("}\n");
   cudaGraphExecDestroy(ge);
   cudaGraphDestroy(g);
   return 0;

@@ -200,3 +200,41 @@ def test_warp_tiles_plan(S, scheme, W):
     # the schedule itself is unchanged: the host replay still covers every point once
     assert S.check_schedule(h.value, 3 * W + 5) == 8 * W * (3 * W + 5) * (1 if scheme == "heat" else 2)
     S.swept_free(h.value)
+
+
+def test_integer_minmod_rule_matches_comparison_form():
+    """The kernels' minmod and wave-speed maximum select by IEEE bit patterns;
+    check that rule against the comparison form (the oracle's) on special
+    values and random doubles and floats of every magnitude."""
+    import numpy as np
+
+    def ref(a, b):
+        if a > 0 and b > 0:
+            return a if a <= b else b
+        if a < 0 and b < 0:
+            return a if a >= b else b
+        return 0.0
+
+    def bits_rule(a, b, itype, mag):
+        ia, ib = np.array([a]).view(itype)[0], np.array([b]).view(itype)[0]
+        same = ((ia ^ ib) >= 0) and (ia & mag) != 0 and (ib & mag) != 0
+        return (a if ia <= ib else b) if same else 0.0
+
+    g = np.random.default_rng(3)
+    for ftype, itype, mag in ((np.float64, np.int64, np.int64(0x7fffffffffffffff)),
+                              (np.float32, np.int32, np.int32(0x7fffffff))):
+        fi = np.finfo(ftype)
+        special = [0.0, -0.0, fi.tiny, -fi.tiny, fi.tiny / 4, -fi.tiny / 4, 1.0, -1.0, fi.max, -fi.max, np.inf, -np.inf]
+        rand = list(g.standard_normal(400) * np.exp(g.uniform(-30, 30, 400)))
+        vals = [ftype(v) for v in special + rand]
+        for a in vals[:60]:
+            for b in vals:
+                r = ftype(ref(a, b))
+                got = ftype(bits_rule(a, b, itype, mag))
+                assert r.tobytes() == got.tobytes(), (a, b, r, got)
+        for a in vals:
+            for b in vals[:40]:
+                if a >= 0 and b >= 0 and not np.signbit(a) and not np.signbit(b):
+                    want = a if a >= b else b
+                    ia, ib = np.array([a]).view(itype)[0], np.array([b]).view(itype)[0]
+                    assert (a if ia >= ib else b) == want
