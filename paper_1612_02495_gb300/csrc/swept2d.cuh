@@ -59,20 +59,16 @@ struct Geom2 {
 
 SW_HD int strip_len(const Geom2& g, int s) { return g.W - 2 * g.R * s; }
 SW_HD int64_t strip_off(const Geom2& g, int s) { return (int64_t)s * g.W - (int64_t)g.R * s * (s - 1); }
-// offset of (side, s, k, p) inside one tile's strip block (< Es, fits 32 bits)
+// offset of (side, s, k, p) inside one tile's strip block (< Es, fits 32 bits);
+// the tile's block starts at tile * Es
 SW_HD int strip_in_tile(const Geom2& g, int side, int s, int k, int p) {
   return side * (2 * g.R) * (int)g.Ph + 2 * g.R * (s * g.W - g.R * s * (s - 1)) + k * strip_len(g, s) + p;
 }
-SW_HD int64_t strip_index(const Geom2& g, int64_t tile, int side, int s, int k, int p) {
-  return tile * g.Es + strip_in_tile(g, side, s, k, p);
-}
 SW_HD int64_t band_off(const Geom2& g, int s) { return (int64_t)g.R * s * (s - 1); }
-// offset of (end, s, k, p) inside one bridge's band block (< Eb)
+// offset of (end, s, k, p) inside one bridge's band block (< Eb); the
+// bridge's block starts at bridge * Eb
 SW_HD int band_in_bridge(const Geom2& g, int end, int s, int k, int p) {
   return end * (2 * g.R) * (int)g.Bh + 2 * g.R * (g.R * s * (s - 1)) + k * (2 * g.R * s) + p;
-}
-SW_HD int64_t band_index(const Geom2& g, int64_t bridge, int end, int s, int k, int p) {
-  return bridge * g.Eb + band_in_bridge(g, end, s, k, p);
 }
 SW_HD int64_t tile_id(const Geom2& g, int64_t tx, int64_t ty) { return wrap_n(ty, g.nty) * g.ntx + wrap_n(tx, g.ntx); }
 // x-bridge between tiles (tx, ty) and (tx+1, ty); y-bridge between (tx, ty) and (tx, ty+1)
