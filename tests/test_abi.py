@@ -238,3 +238,27 @@ def test_integer_minmod_rule_matches_comparison_form():
                     want = a if a >= b else b
                     ia, ib = np.array([a]).view(itype)[0], np.array([b]).view(itype)[0]
                     assert (a if ia >= ib else b) == want
+
+
+def test_schedule_replay_random_configurations(S):
+    """Seeded sweep of the 1D host replay over random schemes, boundary conditions,
+    tile widths, tile counts and step counts (including remainders and a single
+    full pass)."""
+    import numpy as np
+
+    g = np.random.default_rng(20161208)
+    for _ in range(60):
+        scheme = int(g.integers(0, 3))
+        R = 1 if scheme == S.HEAT else 2
+        W = 4 * R * int(g.integers(1, 9))
+        nt = int(g.integers(2, 7))
+        bc = 0 if scheme == S.KS else int(g.integers(0, 2))
+        S_ = 1 if scheme == S.HEAT else 2
+        h = W // (2 * R)
+        nsteps = int(g.choice([1, max(1, h // S_), int(g.integers(1, 4 * h))]))
+        param = 1.4 if scheme == S.EULER else 1.0
+        c = cfg(S, scheme=scheme, n=nt * W, tile_w=W, bc=bc, param0=param)
+        h_ = ctypes.c_void_p()
+        assert S.swept_init(ctypes.byref(c), ctypes.byref(h_)) == S.SWEPT_OK
+        assert S.check_schedule(h_.value, nsteps) == nt * W * nsteps * S_, (scheme, W, nt, bc, nsteps)
+        S.swept_free(h_.value)

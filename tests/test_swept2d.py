@@ -87,6 +87,8 @@ GPU_CASES = [
     (32, 32, 16, 7, 64),        # remainder only
     (16, 16, 8, 1100, 32),      # head + cached body + tail
     (1024, 1024, 32, 40, 0),    # the 2^20-point workload
+    (4096, 4096, 128, 70, 1024),  # the 2^24-point workload, tuned FP32 plan (FP64 caps W at 64)
+    (4096, 4096, 64, 37, 256),
 ]
 
 
@@ -95,6 +97,9 @@ GPU_CASES = [
 @pytest.mark.parametrize("nx,ny,W,nsteps,threads", GPU_CASES)
 def test_swept2d_parity(S, dtype, nx, ny, W, nsteps, threads):
     import torch
+
+    if dtype == np.float64 and W > 64:
+        pytest.skip("FP64 tiles are at most 64 wide (shared memory)")
 
     p = inputs.heat2d_problem(nx=nx, ny=ny, dtype=dtype)
     code = S.F64 if dtype == np.float64 else S.F32
@@ -144,3 +149,15 @@ def test_small_divmod_argument_is_exact():
         rb = np.float32(1.0) / np.float32(b)
         q = ((a.astype(np.float32) + np.float32(0.5)) * rb).astype(np.int64)
         assert np.array_equal(q, np.arange(0, 1025) // b), b
+
+
+def test_schedule2d_replay_random_configurations(S):
+    """Seeded sweep of the 2D host replay over random grids (tile counts 2..5 per axis),
+    tile widths 8..32 and step counts (full half cycles, remainders, both)."""
+    g = np.random.default_rng(20161208)
+    for _ in range(25):
+        W = int(g.choice([8, 12, 16, 20, 24, 32]))
+        ntx, nty = int(g.integers(2, 6)), int(g.integers(2, 6))
+        h = W // 2
+        nsteps = int(g.choice([int(g.integers(1, h)), h, int(g.integers(h + 1, 5 * h))]))
+        assert S.check_schedule2d(S.F64, ntx * W, nty * W, W, nsteps) == ntx * W * nty * W * nsteps

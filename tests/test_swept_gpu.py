@@ -445,3 +445,24 @@ def test_euler_pair_flux_parity(S, dtype, n, W, threads, nsteps, bc, mode):
     assert np.array_equal(got, ref)
     pair.close()
     one.close()
+
+
+def test_euler_large_persistent(S):
+    """Euler Sod at 2^20 cells with the tuned persistent plan (tile 512): equal to
+    classic and the oracle bit for bit after 60 steps."""
+    import torch
+
+    n, nsteps = 1 << 20, 60
+    pr = inputs.euler_problem(n=n)
+    sol = S.Solver(S.EULER, S.F64, n, pr["dx"], pr["dt"], pr["gamma"], bc=1, tile_w=512, threads=128, persistent=1)
+    u = torch.from_numpy(pr["U0"]).cuda()
+    v = u.clone()
+    sol.step(u, nsteps)
+    sol.classic(v, nsteps)
+    torch.cuda.synchronize()
+    sol.sync_status()
+    got = u.cpu().numpy()
+    assert np.array_equal(got, v.cpu().numpy())
+    ref = oracle.euler(pr["U0"], pr["dx"], pr["dt"], pr["gamma"], nsteps, bc=1, threads=THREADS)
+    assert np.array_equal(got, ref)
+    sol.close()
