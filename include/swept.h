@@ -253,7 +253,10 @@ swept_status swept_profile_passes(swept_handle* h, void* u_dev, int64_t nsteps, 
  * no counterpart; it is swept_step_n with the edge buffers in one fixed 8 MiB
  * device array inside the library instead of a bound workspace, and without a
  * handle, graph or stream of its own.
- *   cfg      as for swept_init, except that tile_w must be set (> 0)
+ *   cfg      as for swept_init, except that tile_w must be set (> 0); the
+ *            launch options chunk, persistent, cluster and warp_tiles are
+ *            ignored (one launch per pass, tiers in shared memory, one point
+ *            per thread per trip), which changes no result
  *   u_dev    caller-owned state (layout above), advanced nsteps in place
  * The grid must fit the array: 4 * n * C * sizeof(value) <= 8 MiB (n <= 2^18 for
  * FP64 heat/KS, 2^19 for FP32); larger grids return SWEPT_ENOMEM_WORKSPACE and

@@ -19,7 +19,8 @@
  * handle owns host memory, a private capture stream and cached CUDA graphs.
  * Every compute call is asynchronous on the caller's stream and returns a
  * status; nothing throws across the ABI.  swept2d_last_error describes the
- * last failure of a handle.
+ * last failure of a handle.  A handle is not thread-safe: calls on one handle
+ * must not overlap.
  */
 #ifndef SWEPT2D_H
 #define SWEPT2D_H
