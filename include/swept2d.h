@@ -7,7 +7,7 @@
  * extension for the 2D heat equation on square cells,
  *   T'_{i,j} = Fo (T_{i-1,j} + T_{i+1,j} + T_{i,j-1} + T_{i,j+1}) + (1 - 4 Fo) T_{i,j},
  *   Fo = alpha dt / dx^2,
- * the 2D form of Eq. HeatDisc, on a periodic nx x ny grid.  As in 1D, the
+ * the 2D form of Eq. HeatDisc, on an nx x ny grid, periodic or insulated.  As in 1D, the
  * swept decomposition does not change the scheme: swept2d_step_n and
  * classic2d_step_n produce the same values bit for bit.
  *
@@ -37,7 +37,9 @@ extern "C" {
 /*
  * Problem and launch configuration.
  *   dtype    SWEPT_F32 or SWEPT_F64
- *   bc       SWEPT_BC_PERIODIC (the only boundary of the 2D solver)
+ *   bc       SWEPT_BC_PERIODIC, or SWEPT_BC_REFLECTIVE: insulated ends, mirror
+ *            walls at -1/2 and n - 1/2 on both axes (cell -1 reads cell 0, cell n
+ *            reads cell n - 1)
  *   nx, ny   grid points along x and y: multiples of tile_w, at least two tiles
  *            per axis, ny <= 65535
  *   dx, dt   grid spacing (both axes) and timestep; alpha the diffusivity.

@@ -189,7 +189,7 @@ cudaError_t issue_classic_t(swept2d_handle* h, T* u, int64_t k0, int64_t k1, int
   for (int64_t m = k0; m < k1; ++m) {
     const T* in = (m & 1) ? tmp : u;
     T* out = (m & 1) ? u : tmp;
-    swept2d::k_classic2d<T><<<grid, 256, 0, s>>>(g.nx, g.ny, k, in, out);
+    swept2d::k_classic2d<T><<<grid, 256, 0, s>>>(g.nx, g.ny, g.bc, k, in, out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -211,7 +211,7 @@ swept_status swept2d_init(const swept2d_config* cfg, swept2d_handle** out) {
   if (!cfg || !out) return SWEPT_EINVAL;
   *out = nullptr;
   if (cfg->dtype != SWEPT_F32 && cfg->dtype != SWEPT_F64) return SWEPT_EINVAL;
-  if (cfg->bc != SWEPT_BC_PERIODIC) return SWEPT_EINVAL;
+  if (cfg->bc != SWEPT_BC_PERIODIC && cfg->bc != SWEPT_BC_REFLECTIVE) return SWEPT_EINVAL;
   if (!(cfg->dx > 0) || !(cfg->dt > 0) || !(cfg->alpha > 0)) return SWEPT_EINVAL;
   if (cfg->nx < 16 || cfg->ny < 16 || cfg->ny > 65535) return SWEPT_EINVAL;
   const int W = cfg->tile_w > 0 ? cfg->tile_w : choose_tile(cfg->nx, cfg->ny, cfg->dtype);
@@ -237,6 +237,7 @@ swept_status swept2d_init(const swept2d_config* cfg, swept2d_handle** out) {
   g.Bh = swept2d::band_off(g, g.h);
   g.Es = 4 * 2 * g.R * g.Ph;
   g.Eb = 2 * 2 * g.R * g.Bh;
+  g.bc = cfg->bc;
   h->smem = (size_t)2 * g.M * g.M * h->value_bytes;
   if (h->smem > (size_t)kSmemOptin) {
     delete h;

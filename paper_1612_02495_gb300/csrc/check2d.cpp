@@ -135,17 +135,31 @@ struct Host2Ctx {
     sim.note(sim.ab, (size_t)e, block, true, "bands");
     sim.b[(size_t)e] = cell(r, lx, ly);
   }
+  // The grid point the stencil of (x, y) (in [0, n)) reads at offset (dx, dy),
+  // from the boundary rule itself (independent of the window arithmetic):
+  // periodic wraps; mirror walls at -1/2 and n - 1/2 reflect -1 to 0 and n to n - 1.
+  int64_t physical_neighbour(int64_t x, int64_t y, int dx, int dy) const {
+    auto axis = [&](int64_t v, int64_t n) {
+      if (g.bc == 0) return wrap_n(v, n);
+      if (v < 0) return -1 - v;
+      if (v >= n) return 2 * n - 1 - v;
+      return v;
+    };
+    return axis(y + dy, g.ny) * g.nx + axis(x + dx, g.nx);
+  }
   void level(int s, int base, int x0, int x1, int y0, int y1, int64_t ox, int64_t oy) {
     const int64_t L = base_level + base + s;
     const int row = s & 1;
     static const int dxs[5] = {0, -1, 1, 0, 0}, dys[5] = {0, 0, 0, -1, 1};
+    const int wx = axis_wall(g.bc, g.nx, ox, g.M), wy = axis_wall(g.bc, g.ny, oy, g.M);
     char m[220];
     for (int ly = y0; ly < y1; ++ly)
       for (int lx = x0; lx < x1; ++lx) {
         const int64_t gx = ox + lx, gy = oy + ly;
         for (int d = 0; d < 5; ++d) {
-          const Tag t = cell(row ^ 1, lx + dxs[d], ly + dys[d]);
-          const int64_t want = gp(gx + dxs[d], gy + dys[d]);
+          // the window cell the kernels read: across a wall, the mirror image
+          const Tag t = cell(row ^ 1, swept::nbr(lx, dxs[d], wx), swept::nbr(ly, dys[d], wy));
+          const int64_t want = physical_neighbour(wrap_once(gx, g.nx), wrap_once(gy, g.ny), dxs[d], dys[d]);
           if (t.p != want || t.lvl != L - 1) {
             snprintf(m, sizeof m,
                      "block %lld level %lld point (%lld, %lld): input (%d, %d) holds (point %lld, level %lld), "

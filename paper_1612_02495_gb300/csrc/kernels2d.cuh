@@ -83,29 +83,47 @@ struct Dev2Ctx {
   // level s on the local rectangle [x0, x1) x [y0, y1): row s & 1 from row
   // (s - 1) & 1.  The rectangle's points are spread flat over the block (point
   // i = y w + x to thread i mod blockDim), so narrow regions (bridges, small
-  // corners) still fill whole warps.
-  __device__ __forceinline__ void level(int s, int, int x0, int x1, int y0, int y1, int64_t, int64_t) {
+  // corners) still fill whole warps.  A window that holds a mirror wall takes
+  // the neighbours of its points through swept::nbr (a block-uniform branch).
+  __device__ __forceinline__ void level(int s, int, int x0, int x1, int y0, int y1, int64_t ox, int64_t oy) {
     const int M = g.M;
     const T* in = sm + (int64_t)((s & 1) ^ 1) * M * M;
     T* out = sm + (int64_t)(s & 1) * M * M;
     const int w = x1 - x0, n = w * (y1 - y0);
     const int t = (int)threadIdx.x, nt = (int)blockDim.x;
+    const int wx = axis_wall(g.bc, g.nx, ox, M), wy = axis_wall(g.bc, g.ny, oy, M);
     if (t < n) {
       int y, x, dy, dx;
       const float rw = recip_small(w);
       divmod_small(t, w, rw, y, x);
       divmod_small(nt, w, rw, dy, dx);
-      T* o = out + (y0 + y) * M + x0;
-      const T* c = in + (y0 + y) * M + x0;
-      for (int i = t; i < n; i += nt) {
-        o[x] = heat2d_point<T>(c + x, M, k);
-        x += dx;
-        o += dy * M;
-        c += dy * M;
-        if (x >= w) {
-          x -= w;
-          o += M;
-          c += M;
+      if (wx == swept::NO_WALL && wy == swept::NO_WALL) {
+        T* o = out + (y0 + y) * M + x0;
+        const T* c = in + (y0 + y) * M + x0;
+        for (int i = t; i < n; i += nt) {
+          o[x] = heat2d_point<T>(c + x, M, k);
+          x += dx;
+          o += dy * M;
+          c += dy * M;
+          if (x >= w) {
+            x -= w;
+            o += M;
+            c += M;
+          }
+        }
+      } else {
+        for (int i = t; i < n; i += nt) {
+          const int lx = x0 + x, ly = y0 + y;
+          const T* row = in + ly * M;
+          const T sx = add_rn(row[swept::nbr(lx, -1, wx)], row[swept::nbr(lx, 1, wx)]);
+          const T sy = add_rn(in[swept::nbr(ly, -1, wy) * M + lx], in[swept::nbr(ly, 1, wy) * M + lx]);
+          out[ly * M + lx] = fma_rn(k.fo, add_rn(sx, sy), mul_rn(k.c1, row[lx]));
+          x += dx;
+          y += dy;
+          if (x >= w) {
+            x -= w;
+            ++y;
+          }
         }
       }
     }
@@ -139,15 +157,17 @@ __global__ void __launch_bounds__(1024) k_octa2d(Geom2 g, Heat2dK<T> k, T* u, co
   run_octa(cx, g, b % g.ntx, b / g.ntx, odd, mode, hh);
 }
 
-// classic: one step of the whole grid, global memory in and out (periodic)
+// classic: one step of the whole grid, global memory in and out; periodic
+// (bc 0) or mirror walls at -1/2 and n - 1/2 (bc 1: cell -1 reads cell 0, cell
+// n reads cell n - 1)
 template <typename T>
-__global__ void __launch_bounds__(256) k_classic2d(int64_t nx, int64_t ny, Heat2dK<T> k, const T* __restrict__ in,
-                                                   T* __restrict__ out) {
+__global__ void __launch_bounds__(256) k_classic2d(int64_t nx, int64_t ny, int bc, Heat2dK<T> k,
+                                                   const T* __restrict__ in, T* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t j = blockIdx.y;
   if (i >= nx) return;
-  const int64_t iw = i == 0 ? nx - 1 : i - 1, ie = i == nx - 1 ? 0 : i + 1;
-  const int64_t js = j == 0 ? ny - 1 : j - 1, jn = j == ny - 1 ? 0 : j + 1;
+  const int64_t iw = i == 0 ? (bc ? 0 : nx - 1) : i - 1, ie = i == nx - 1 ? (bc ? nx - 1 : 0) : i + 1;
+  const int64_t js = j == 0 ? (bc ? 0 : ny - 1) : j - 1, jn = j == ny - 1 ? (bc ? ny - 1 : 0) : j + 1;
   const T sx = add_rn(in[j * nx + iw], in[j * nx + ie]);
   const T sy = add_rn(in[js * nx + i], in[jn * nx + i]);
   out[j * nx + i] = fma_rn(k.fo, add_rn(sx, sy), mul_rn(k.c1, in[j * nx + i]));

@@ -55,7 +55,20 @@ struct Geom2 {
   int64_t Bh;        // sum over s < h of the band length 2Rs
   int64_t Es;        // values per tile in a strip buffer: 4 sides * 2R * Ph
   int64_t Eb;        // values per bridge in the band buffer: 2 ends * 2R * Bh
+  int bc;            // 0 periodic, 1 mirror walls at -1/2 and n - 1/2 on both axes (insulated)
 };
+
+// Along one axis of n points, the local index of the first point after a
+// mirror wall (a multiple of n) inside the window [origin, origin + M), or
+// NO_WALL (periodic, or no wall inside).  A window is shorter than n, so it
+// holds at most one wall per axis; the points on its two sides are the two
+// ends of the domain, and a stencil read across the wall takes the mirror
+// image on the reader's own side (swept::nbr).
+SW_HD int axis_wall(int bc, int64_t n, int64_t origin, int M) {
+  if (bc == 0) return swept::NO_WALL;
+  const int64_t xw = (swept::floor_div(origin, n) + 1) * n;
+  return xw < origin + M ? (int)(xw - origin) : swept::NO_WALL;
+}
 
 SW_HD int strip_len(const Geom2& g, int s) { return g.W - 2 * g.R * s; }
 SW_HD int64_t strip_off(const Geom2& g, int s) { return (int64_t)s * g.W - (int64_t)g.R * s * (s - 1); }

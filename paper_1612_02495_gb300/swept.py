@@ -438,10 +438,10 @@ class Solver2D:
     """A 2D swept handle plus its workspace (a torch uint8 tensor on the current
     device).  States are contiguous CUDA tensors of shape (ny, nx)."""
 
-    def __init__(self, dtype, nx, ny, dx, dt, alpha, tile_w=0, threads=0):
+    def __init__(self, dtype, nx, ny, dx, dt, alpha, tile_w=0, threads=0, bc=BC_PERIODIC):
         import torch
 
-        self.cfg = make_config2d(dtype, nx, ny, dx, dt, alpha, tile_w, threads)
+        self.cfg = make_config2d(dtype, nx, ny, dx, dt, alpha, tile_w, threads, bc)
         h = _H()
         st = swept2d_init(ctypes.byref(self.cfg), ctypes.byref(h))
         if st != SWEPT_OK:
@@ -493,10 +493,10 @@ class Solver2D:
             pass
 
 
-def check_schedule2d(dtype, nx, ny, tile_w, nsteps, threads=0):
+def check_schedule2d(dtype, nx, ny, tile_w, nsteps, threads=0, bc=BC_PERIODIC):
     """Host-only symbolic replay of the 2D launch sequence (no GPU): returns the
     number of point updates, raises SweptError with the first violation."""
-    cfg = make_config2d(dtype, nx, ny, 1.0, 0.2, 1.0, tile_w, threads)
+    cfg = make_config2d(dtype, nx, ny, 1.0, 0.2, 1.0, tile_w, threads, bc)
     h = _H()
     st = swept2d_init(ctypes.byref(cfg), ctypes.byref(h))
     if st != SWEPT_OK:

@@ -29,7 +29,7 @@ def S():
 
 @pytest.mark.parametrize("bad", [
     dict(nx=100), dict(ny=20), dict(tile_w=12), dict(tile_w=6), dict(tile_w=128),  # 128 > 64 for FP64
-    dict(nx=64, tile_w=64), dict(threads=48), dict(dx=0.0), dict(dt=-1.0), dict(alpha=0.0), dict(bc=1),
+    dict(nx=64, tile_w=64), dict(threads=48), dict(dx=0.0), dict(dt=-1.0), dict(alpha=0.0), dict(bc=2),
     dict(dtype=5), dict(ny=70000, nx=64, tile_w=8),
 ])
 def test_init2d_rejects_invalid(S, bad):
@@ -66,9 +66,10 @@ SCHEDULES = [
 ]
 
 
+@pytest.mark.parametrize("bc", [0, 1])
 @pytest.mark.parametrize("nx,ny,W,nsteps", SCHEDULES)
-def test_schedule2d_replay(S, nx, ny, W, nsteps):
-    assert S.check_schedule2d(S.F64, nx, ny, W, nsteps) == nx * ny * nsteps
+def test_schedule2d_replay(S, nx, ny, W, nsteps, bc):
+    assert S.check_schedule2d(S.F64, nx, ny, W, nsteps, bc=bc) == nx * ny * nsteps
 
 
 def test_schedule2d_long_run_with_cached_body(S):
@@ -112,6 +113,34 @@ def test_swept2d_parity(S, dtype, nx, ny, W, nsteps, threads):
     got = u.cpu().numpy()
     assert np.array_equal(got, v.cpu().numpy()), "swept2d != classic2d"
     ref = oracle.heat2d(p["u0"], p["dx"], p["dt"], p["alpha"], nsteps, threads=8)
+    assert np.array_equal(got, ref), "swept2d != oracle"
+    sol.close()
+
+
+MIRROR_CASES = [
+    # nx, ny, W, nsteps
+    (64, 48, 16, 37), (96, 64, 32, 100), (16, 16, 8, 1100), (1024, 1024, 32, 40), (128, 128, 64, 70),
+]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("nx,ny,W,nsteps", MIRROR_CASES)
+def test_swept2d_insulated_parity(S, dtype, nx, ny, W, nsteps):
+    """Insulated (mirror) walls on both axes: swept2d == classic2d == the oracle bit for bit."""
+    import torch
+
+    p = inputs.heat2d_problem(nx=nx, ny=ny, dtype=dtype)
+    code = S.F64 if dtype == np.float64 else S.F32
+    sol = S.Solver2D(code, nx, ny, p["dx"], p["dt"], p["alpha"], tile_w=W, bc=S.BC_REFLECTIVE)
+    u = torch.from_numpy(p["u0"]).cuda()
+    v = u.clone()
+    sol.step(u, nsteps)
+    sol.classic(v, nsteps)
+    torch.cuda.synchronize()
+    got = u.cpu().numpy()
+    assert np.array_equal(got, v.cpu().numpy()), "swept2d != classic2d"
+    ref = oracle.heat2d(p["u0"], p["dx"], p["dt"], p["alpha"], nsteps, bc=oracle.BC_MIRROR, threads=8)
     assert np.array_equal(got, ref), "swept2d != oracle"
     sol.close()
 
@@ -160,4 +189,5 @@ def test_schedule2d_replay_random_configurations(S):
         ntx, nty = int(g.integers(2, 6)), int(g.integers(2, 6))
         h = W // 2
         nsteps = int(g.choice([int(g.integers(1, h)), h, int(g.integers(h + 1, 5 * h))]))
-        assert S.check_schedule2d(S.F64, ntx * W, nty * W, W, nsteps) == ntx * W * nty * W * nsteps
+        bc = int(g.integers(0, 2))
+        assert S.check_schedule2d(S.F64, ntx * W, nty * W, W, nsteps, bc=bc) == ntx * W * nty * W * nsteps
