@@ -8,6 +8,7 @@
 #include <new>
 #include <string>
 
+#include "graph_cache.h"
 #include "kernels2d.cuh"
 #include "swept2d.h"
 
@@ -60,47 +61,13 @@ int choose_tile(int64_t nx, int64_t ny, int dtype) {
   return 0;
 }
 
-std::string key_of(const char* kind, const void* u, int64_t a) {
-  char buf[128];
-  snprintf(buf, sizeof buf, "%s:%p:%lld", kind, u, (long long)a);
-  return buf;
-}
 
 swept_status run_graph(swept2d_handle* h, const std::string& key, cudaStream_t user,
                        const std::function<cudaError_t(cudaStream_t)>& issue) {
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  cudaError_t e = cudaStreamIsCapturing(user, &cs);
-  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamIsCapturing");
-  if (cs != cudaStreamCaptureStatusNone) {
-    e = issue(user);
-    return e == cudaSuccess ? SWEPT_OK : cuda_fail(h, e, "kernel launch");
-  }
-  auto it = h->graphs.find(key);
-  if (it == h->graphs.end()) {
-    e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamBeginCapture");
-    cudaError_t le = issue(h->cap);
-    cudaGraph_t graph = nullptr;
-    e = cudaStreamEndCapture(h->cap, &graph);
-    if (le != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      return cuda_fail(h, le, "kernel launch during capture");
-    }
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
-    cudaGraphExec_t exec = nullptr;
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
-    it = h->graphs.emplace(key, exec).first;
-  }
-  e = cudaGraphLaunch(it->second, user);
-  return e == cudaSuccess ? SWEPT_OK : cuda_fail(h, e, "cudaGraphLaunch");
+  return swept_graphs::run(h, key, user, issue);
 }
-
-void drop_graphs(swept2d_handle* h) {
-  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
-  h->graphs.clear();
-}
+void drop_graphs(swept2d_handle* h) { swept_graphs::drop(h); }
+using swept_graphs::key_of;
 
 template <typename T>
 cudaError_t prepare_t(size_t smem) {
