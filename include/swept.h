@@ -271,6 +271,21 @@ swept_status swept_step_n_static(const swept_config* cfg, void* u_dev, int64_t n
 /* Plan report. */
 swept_status swept_get_plan(const swept_handle* h, swept_plan_info* out);
 
+/* Options of the persistent single-problem kernel (persistent = 1); the paper
+ * has no counterpart.  Setting one drops the handle's cached graphs.
+ *   SWEPT_OPT_SPIN_LIMIT  polls a block makes while waiting for an input tile
+ *                         before it gives up and the solve reports
+ *                         SWEPT_ETIMEOUT through swept_sync_status (default
+ *                         2^24, each poll sleeping about 0.1 us; 1 .. 2^32 - 1)
+ *   SWEPT_OPT_START_ITEM  first queue item the kernel claims (default 0).  A
+ *                         value > 0 skips the items before it, so later items
+ *                         wait for tiles nobody computes: it exists to exercise
+ *                         the timeout path without a GPU fault (the state is
+ *                         then not a valid solve).
+ * Errors: SWEPT_EINVAL (unknown option or value out of range). */
+enum { SWEPT_OPT_SPIN_LIMIT = 1, SWEPT_OPT_START_ITEM = 2 };
+swept_status swept_set_option(swept_handle* h, int32_t option, int64_t value);
+
 /* Synchronize `stream`, then read and clear the device-side error word.
  * Returns SWEPT_OK, SWEPT_ETIMEOUT or SWEPT_EDEVICE. */
 swept_status swept_sync_status(swept_handle* h, void* stream);

@@ -437,7 +437,8 @@ swept_status swept_step_n(swept_handle* h, void* u_dev, int64_t nsteps, void* st
       if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, 16, cs);
       if (e == cudaSuccess)
         e = h->impl->persist(g, h->k, u_dev, h->ws + h->off_e0, h->ws + h->off_e1, n_sub, done,
-                             (unsigned long long*)ctl, (int*)(ctl + 8), 1u << 24, blocks, h->threads, h->smem, cs);
+                             (unsigned long long*)ctl, (int*)(ctl + 8), h->spin_limit, h->start_item, blocks,
+                             h->threads, h->smem, cs);
       // a wait that ran out is latched into the handle's status word
       if (e == cudaSuccess) {
         swept::k_latch_error<<<1, 1, 0, cs>>>((const int*)(ctl + 8), (int*)(h->ws + h->off_status));
@@ -649,6 +650,21 @@ swept_status swept_sync_status(swept_handle* h, void* stream) {
   if (e != cudaSuccess) return cuda_fail(h, e, "swept_sync_status");
   if (word == 0) return SWEPT_OK;
   return fail(h, word == SWEPT_ETIMEOUT ? SWEPT_ETIMEOUT : SWEPT_EDEVICE, "device-side error word set");
+}
+
+swept_status swept_set_option(swept_handle* h, int32_t option, int64_t value) {
+  if (!h) return SWEPT_EINVAL;
+  if (option == SWEPT_OPT_SPIN_LIMIT) {
+    if (value < 1 || value > 0xffffffffLL) return fail(h, SWEPT_EINVAL, "spin limit outside [1, 2^32)");
+    h->spin_limit = (uint32_t)value;
+  } else if (option == SWEPT_OPT_START_ITEM) {
+    if (value < 0) return fail(h, SWEPT_EINVAL, "start item < 0");
+    h->start_item = value;
+  } else {
+    return fail(h, SWEPT_EINVAL, "unknown option");
+  }
+  drop_graphs(h);  // captured persistent launches carry the options
+  return SWEPT_OK;
 }
 
 swept_status swept_check_schedule(swept_handle* h, int64_t nsteps, int64_t* computed_out) {

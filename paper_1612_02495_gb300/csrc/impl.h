@@ -29,8 +29,8 @@ struct SchemeImpl {
   cudaError_t (*copy)(int64_t n, const void* src, void* dst, cudaStream_t s);
   // persistent single-problem kernel over n_sub sub-timesteps (grid = blocks)
   cudaError_t (*persist)(const Geom& g, const void* k, void* u, void* e0, void* e1, int64_t n_sub, int* done,
-                         unsigned long long* queue, int* error, uint32_t spin_limit, int blocks, int threads,
-                         size_t smem, cudaStream_t s);
+                         unsigned long long* queue, int* error, uint32_t spin_limit, int64_t start_item, int blocks,
+                         int threads, size_t smem, cudaStream_t s);
   // co-resident blocks per SM of the persistent kernel (variant P = Geom::P)
   int (*persist_blocks_per_sm)(int P, int threads, size_t smem);
   // whole solve in one cluster of g.nt (<= 16) blocks, edges through DSMEM

@@ -69,8 +69,8 @@ struct Launch {
     return cudaGetLastError();
   }
   static cudaError_t persist(const Geom& g, const void* k, void* u, void* e0, void* e1, int64_t n_sub, int* done,
-                             unsigned long long* queue, int* error, uint32_t spin_limit, int blocks, int threads,
-                             size_t smem, cudaStream_t s) {
+                             unsigned long long* queue, int* error, uint32_t spin_limit, int64_t start_item,
+                             int blocks, int threads, size_t smem, cudaStream_t s) {
     return with_p(g.P, [&](auto pc) {
       constexpr int P = decltype(pc)::value;
       if (smem > 48 * 1024) {
@@ -78,7 +78,7 @@ struct Launch {
             cudaFuncSetAttribute(k_swept_persist<T, Op, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
       }
-      PersistCtl c{done, queue, error, spin_limit};
+      PersistCtl c{done, queue, error, spin_limit, start_item};
       k_swept_persist<T, Op, P><<<blocks, threads, smem, s>>>(g, kc(k), (T*)u, (T*)e0, (T*)e1, n_sub, c);
       return cudaGetLastError();
     });

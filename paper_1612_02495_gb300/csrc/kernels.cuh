@@ -516,6 +516,7 @@ struct PersistCtl {
   unsigned long long* queue;  // next item
   int* error;                 // SWEPT_ETIMEOUT (4) once a wait ran out
   uint32_t spin_limit;
+  int64_t start_item;         // the first item claimed (0; > 0 only to exercise the timeout path)
 };
 
 template <typename T, class Op>
@@ -569,7 +570,7 @@ __global__ void __launch_bounds__(P > 0 ? 32 : 1024, P > 0 ? 16 : 1) k_swept_per
   const int64_t total = (int64_t)(main_passes + (rem > 0 ? 2 : 0)) * g.nt;
   T* eb[2] = {e0, e1};
   for (;;) {
-    if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(ctl.queue, 1ULL);
+    if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(ctl.queue, 1ULL) + ctl.start_item;
     __syncthreads();
     const int64_t item = s_item;
     if (item >= total) break;

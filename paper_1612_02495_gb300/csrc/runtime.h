@@ -28,6 +28,8 @@ struct swept_handle {
   bool persistent = false;
   bool cluster = false;
   int persist_blocks = 0;  // co-resident blocks of the persistent kernel (0 = not yet queried)
+  uint32_t spin_limit = 1u << 24;  // polls a persistent block waits for an input tile (swept_set_option)
+  int64_t start_item = 0;          // first queue item the persistent kernel claims (swept_set_option)
   // CUDA graphs cached by key; captured on a private stream
   cudaStream_t cap = nullptr;
   std::map<std::string, cudaGraphExec_t> graphs;

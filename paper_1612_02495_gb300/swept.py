@@ -74,6 +74,8 @@ swept_profile_passes = _sig("swept_profile_passes", [_H, _P, _I64, _P, ctypes.PO
                                                      ctypes.POINTER(_I64)])
 swept_step_n_static = _sig("swept_step_n_static", [ctypes.POINTER(swept_config), _P, _I64, _P])
 swept_get_plan = _sig("swept_get_plan", [_H, ctypes.POINTER(swept_plan_info)])
+SWEPT_OPT_SPIN_LIMIT, SWEPT_OPT_START_ITEM = 1, 2
+swept_set_option = _sig("swept_set_option", [_H, _I32, _I64])
 
 
 class swept_batch_problem(ctypes.Structure):
@@ -250,6 +252,10 @@ class Solver:
 
     def check_schedule(self, nsteps):
         return check_schedule(self.h, nsteps)
+
+    def set_option(self, option, value):
+        """swept_set_option (persistent kernel: SWEPT_OPT_SPIN_LIMIT, SWEPT_OPT_START_ITEM)."""
+        check(swept_set_option(self.h, int(option), int(value)), self.h, "swept_set_option")
 
     def close(self):
         if self.h:

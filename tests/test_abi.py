@@ -262,3 +262,14 @@ def test_schedule_replay_random_configurations(S):
         assert S.swept_init(ctypes.byref(c), ctypes.byref(h_)) == S.SWEPT_OK
         assert S.check_schedule(h_.value, nsteps) == nt * W * nsteps * S_, (scheme, W, nt, bc, nsteps)
         S.swept_free(h_.value)
+
+
+@pytest.mark.parametrize("option,value", [(0, 5), (3, 1), (1, 0), (1, 1 << 33), (2, -1)])
+def test_set_option_rejects_invalid(S, option, value):
+    c = cfg(S, n=1024, tile_w=64, persistent=1)
+    h = ctypes.c_void_p()
+    assert S.swept_init(ctypes.byref(c), ctypes.byref(h)) == S.SWEPT_OK
+    assert S.swept_set_option(h.value, option, value) == S.SWEPT_EINVAL
+    assert S.swept_set_option(h.value, S.SWEPT_OPT_SPIN_LIMIT, 5000) == S.SWEPT_OK
+    assert S.swept_set_option(h.value, S.SWEPT_OPT_START_ITEM, 3) == S.SWEPT_OK
+    S.swept_free(h.value)

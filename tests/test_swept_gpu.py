@@ -466,3 +466,34 @@ def test_euler_large_persistent(S):
     ref = oracle.euler(pr["U0"], pr["dx"], pr["dt"], pr["gamma"], nsteps, bc=1, threads=THREADS)
     assert np.array_equal(got, ref)
     sol.close()
+
+
+def test_persistent_timeout_path(S):
+    """Failure detection without a GPU fault: the persistent kernel's queue starts
+    one pass layer late, so every item waits for tiles no block computes.  Each
+    bounded wait gives up, SWEPT_ETIMEOUT reaches the host through
+    swept_sync_status, and the context stays usable: a normal solve right after
+    equals classic bit for bit."""
+    import torch
+
+    n, W = 1 << 14, 256
+    p = inputs.ks_problem(n=n)
+    sol = S.Solver(S.KS, S.F64, n, p["dx"], p["dt"], p["nu"], tile_w=W, threads=128, persistent=1)
+    u0 = torch.from_numpy(p["u0"]).cuda()
+    u = u0.clone()
+    sol.set_option(S.SWEPT_OPT_SPIN_LIMIT, 1000)
+    sol.set_option(S.SWEPT_OPT_START_ITEM, n // W)
+    sol.step(u, 200)
+    with pytest.raises(S.SweptError) as e:
+        sol.sync_status()
+    assert e.value.status == S.SWEPT_ETIMEOUT
+    sol.set_option(S.SWEPT_OPT_START_ITEM, 0)
+    sol.set_option(S.SWEPT_OPT_SPIN_LIMIT, 1 << 24)
+    u.copy_(u0)
+    v = u0.clone()
+    sol.step(u, 200)
+    sol.classic(v, 200)
+    torch.cuda.synchronize()
+    sol.sync_status()
+    assert torch.equal(u, v)
+    sol.close()
