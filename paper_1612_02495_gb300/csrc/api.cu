@@ -12,6 +12,7 @@
 #include "graph_cache.h"
 #include "kernels.cuh"
 #include "runtime.h"
+#include "trace.h"
 #include "swept_phases.cuh"
 
 using swept::Geom;
@@ -410,6 +411,7 @@ swept_status swept_bind_workspace(swept_handle* h, void* ws_dev, size_t bytes) {
 }
 
 swept_status swept_step_n(swept_handle* h, void* u_dev, int64_t nsteps, void* stream) {
+  const swept_trace::Range trace_range("swept_step_n");
   swept_status st = check_ready(h, u_dev, nsteps);
   if (st != SWEPT_OK || nsteps == 0) return st;
   const cudaStream_t s = (cudaStream_t)stream;
@@ -471,6 +473,7 @@ swept_status swept_step_n(swept_handle* h, void* u_dev, int64_t nsteps, void* st
 }
 
 swept_status classic_step_n(swept_handle* h, void* u_dev, int64_t nsteps, void* stream) {
+  const swept_trace::Range trace_range("classic_step_n");
   swept_status st = check_ready(h, u_dev, nsteps);
   if (st != SWEPT_OK || nsteps == 0) return st;
   const cudaStream_t s = (cudaStream_t)stream;
@@ -495,6 +498,7 @@ swept_status classic_step_n(swept_handle* h, void* u_dev, int64_t nsteps, void* 
 
 swept_status swept_run_host(swept_handle* h, const void* u_host_in, void* u_host_out, void* u_dev, int64_t nsteps,
                             int32_t use_swept, void* stream) {
+  const swept_trace::Range trace_range("swept_run_host");
   if (!h) return SWEPT_EINVAL;
   if (!u_host_in || !u_host_out) return fail(h, SWEPT_EINVAL, "host buffer is NULL");
   swept_status st = check_ready(h, u_dev, nsteps);
@@ -520,6 +524,7 @@ swept_status swept_adjoint_ckpt_size(const swept_handle* h, int64_t nsteps, size
 
 swept_status swept_forward_ckpt(swept_handle* h, void* u_dev, int64_t nsteps, void* ckpt_dev, size_t ckpt_bytes,
                                 void* stream) {
+  const swept_trace::Range trace_range("swept_forward_ckpt");
   swept_status st = check_ready(h, u_dev, nsteps);
   if (st != SWEPT_OK) return st;
   AdjPlan a;
@@ -530,6 +535,7 @@ swept_status swept_forward_ckpt(swept_handle* h, void* u_dev, int64_t nsteps, vo
 
 swept_status swept_adjoint(swept_handle* h, const void* u0_dev, const void* gT_dev, int64_t nsteps, void* g_u0_dev,
                            void* g_param_dev, void* ckpt_dev, size_t ckpt_bytes, void* stream) {
+  const swept_trace::Range trace_range("swept_adjoint");
   swept_status st = check_ready(h, g_u0_dev, nsteps);
   if (st != SWEPT_OK) return st;
   if (!gT_dev || !g_param_dev) return fail(h, SWEPT_EINVAL, "gT_dev or g_param_dev is NULL");

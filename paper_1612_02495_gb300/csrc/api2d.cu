@@ -11,6 +11,7 @@
 #include "graph_cache.h"
 #include "kernels2d.cuh"
 #include "swept2d.h"
+#include "trace.h"
 
 using swept2d::Geom2;
 
@@ -248,6 +249,7 @@ swept_status swept2d_bind_workspace(swept2d_handle* h, void* ws_dev, size_t byte
 }
 
 swept_status swept2d_step_n(swept2d_handle* h, void* u_dev, int64_t nsteps, void* stream) {
+  const swept_trace::Range trace_range("swept2d_step_n");
   swept_status st = check_ready(h, u_dev, nsteps);
   if (st != SWEPT_OK || nsteps == 0) return st;
   const cudaStream_t s = (cudaStream_t)stream;
@@ -273,6 +275,7 @@ swept_status swept2d_step_n(swept2d_handle* h, void* u_dev, int64_t nsteps, void
 }
 
 swept_status classic2d_step_n(swept2d_handle* h, void* u_dev, int64_t nsteps, void* stream) {
+  const swept_trace::Range trace_range("classic2d_step_n");
   swept_status st = check_ready(h, u_dev, nsteps);
   if (st != SWEPT_OK || nsteps == 0) return st;
   const cudaStream_t s = (cudaStream_t)stream;

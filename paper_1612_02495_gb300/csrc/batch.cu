@@ -31,6 +31,7 @@
 #include "impl.h"
 #include "ops.cuh"
 #include "swept.h"
+#include "trace.h"
 #include "swept_phases.cuh"
 
 namespace swept {
@@ -473,6 +474,7 @@ swept_status swept_batch_set_option(swept_batch* b, int32_t option, int64_t valu
 }
 
 swept_status swept_batch_run(swept_batch* b, void* u_dev, void* stream) {
+  const swept_trace::Range trace_range("swept_batch_run");
   if (!b || !u_dev) return SWEPT_EINVAL;
   if (!b->ws) return bfail(b, SWEPT_ENOWORKSPACE, "no workspace bound");
   if (b->total_items == 0) return SWEPT_OK;
