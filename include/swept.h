@@ -294,9 +294,14 @@ swept_status swept_sync_status(swept_handle* h, void* stream);
  * arithmetic the kernels use for nsteps full timesteps on symbolic
  * (point, sub-timestep) tags and verifies that every point of every
  * sub-timestep is computed exactly once, only after all of its stencil inputs,
- * and that the final tier is complete.  computed_out (may be NULL) receives the
- * number of point updates performed.  Returns SWEPT_OK or SWEPT_EDEVICE with a
- * message in swept_last_error. */
+ * and that the final tier is complete.  With persistent = 1 it replays the
+ * persistent kernel's item queue instead and also checks the order its waits
+ * guarantee: every read of a state or edge value happens after the item that
+ * wrote it, and every write after the previous writer and all items that read
+ * the previous value (at most 8192 items; larger returns SWEPT_EINVAL).  Without
+ * it, no two blocks of one launch may touch a location one of them writes.
+ * computed_out (may be NULL) receives the number of point updates performed.
+ * Returns SWEPT_OK or SWEPT_EDEVICE with a message in swept_last_error. */
 swept_status swept_check_schedule(swept_handle* h, int64_t nsteps, int64_t* computed_out);
 
 /* Copy the last error message (NUL-terminated, truncated to len). */

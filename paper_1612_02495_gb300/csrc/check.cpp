@@ -10,6 +10,12 @@
 //   - blocks of one launch never touch a global location another block of the
 //     same launch writes (no race between blocks);
 //   - at the end the state holds tier n_sub at every point.
+// For a persistent handle the replay runs the persistent kernel's item queue
+// instead of launches.  Its blocks order themselves only through the waits of
+// persist_deps, so the check there is on the happens-before relation those
+// waits create: every read of a global location must happen after the item
+// that wrote it, and every write after the location's previous writer and
+// every item that read that earlier value.
 #include <stdio.h>
 
 #include <string>
@@ -32,6 +38,13 @@ struct Access {  // per global location, within the current launch
   int64_t reader = -1;  // -2: read by several blocks
 };
 
+struct HbLoc {  // per global location, persistent mode
+  int64_t writer = -1;           // item that wrote the current value (-1: the initial state)
+  std::vector<int64_t> readers;  // items that read the current value
+};
+
+enum Buf { BUF_U = 0, BUF_E0 = 1, BUF_E1 = 2 };
+
 struct Sim {
   Geom g;
   int64_t n_sub = 0;
@@ -42,11 +55,18 @@ struct Sim {
   int64_t stamp = 0;
   int64_t computed = 0;
   std::string err;
+  // persistent mode: item ancestors (bitsets over item ids) and per-location history
+  bool hb_mode = false;
+  std::vector<std::vector<uint64_t>> anc;
+  std::vector<HbLoc> hb[3];
 
   void fail(const std::string& m) {
     if (err.empty()) err = m;
   }
-  void note(std::vector<Access>& a, size_t i, int64_t block, bool write, const char* what) {
+  bool before(int64_t a, int64_t b) const { return a == b || ((anc[(size_t)b][(size_t)(a >> 6)] >> (a & 63)) & 1); }
+  void note(Buf buf, size_t i, int64_t block, bool write, const char* what) {
+    if (hb_mode) return note_hb(buf, i, block, write, what);
+    std::vector<Access>& a = buf == BUF_U ? au : ae[buf - BUF_E0];
     Access& x = a[i];
     if (x.stamp != stamp) x = Access{stamp, -1, -1};
     if (write) {
@@ -65,6 +85,28 @@ struct Sim {
       }
       x.reader = (x.reader == -1 || x.reader == block) ? block : -2;
     }
+  }
+  // `block` is the item id in persistent mode
+  void note_hb(Buf buf, size_t i, int64_t item, bool write, const char* what) {
+    HbLoc& x = hb[buf][i];
+    char b[200];
+    if (x.writer >= 0 && !before(x.writer, item)) {
+      snprintf(b, sizeof b, "item %lld %s %s[%zu] written by item %lld, which it does not wait for", (long long)item,
+               write ? "overwrites" : "reads", what, i, (long long)x.writer);
+      return fail(b);
+    }
+    if (!write) {
+      if (x.readers.empty() || x.readers.back() != item) x.readers.push_back(item);
+      return;
+    }
+    for (int64_t r : x.readers)
+      if (!before(r, item)) {
+        snprintf(b, sizeof b, "item %lld overwrites %s[%zu] that item %lld reads, without waiting for it",
+                 (long long)item, what, i, (long long)r);
+        return fail(b);
+      }
+    x.writer = item;
+    x.readers.clear();
   }
 };
 
@@ -95,24 +137,24 @@ struct HostCtx {
   }
   void load_u(int r, int c, int j, int64_t x) {
     const size_t i = (size_t)(c * g.N + wrap_n(x, g.N));
-    sim.note(sim.au, i, block, false, "u");
+    sim.note(BUF_U, i, block, false, "u");
     cell(r, c, j) = sim.u[i];
   }
   void store_u(int r, int c, int j, int64_t x) {
     const size_t i = (size_t)(c * g.N + wrap_n(x, g.N));
-    sim.note(sim.au, i, block, true, "u");
+    sim.note(BUF_U, i, block, true, "u");
     const Tag t = cell(r, c, j);
     if (t.x != wrap_n(x, g.N)) sim.fail("store_u writes a value of another point");
     sim.u[i] = t;
   }
   void load_edge(int r, int c, int j, int64_t e) {
     if (e < 0 || (size_t)e >= sim.e[ein].size()) return sim.fail("edge index out of range");
-    sim.note(sim.ae[ein], (size_t)e, block, false, "edges");
+    sim.note(ein == 0 ? BUF_E0 : BUF_E1, (size_t)e, block, false, "edges");
     cell(r, c, j) = sim.e[ein][(size_t)e];
   }
   void store_edge(int r, int c, int j, int64_t e) {
     if (e < 0 || (size_t)e >= sim.e[eout].size()) return sim.fail("edge index out of range");
-    sim.note(sim.ae[eout], (size_t)e, block, true, "edges");
+    sim.note(eout == 0 ? BUF_E0 : BUF_E1, (size_t)e, block, true, "edges");
     sim.e[eout][(size_t)e] = cell(r, c, j);
   }
   // The grid point whose value the stencil of point x reads at offset d, from
@@ -170,42 +212,9 @@ struct HostCtx {
 
 }  // namespace
 
-swept_status check_schedule(swept_handle* h, int64_t nsteps, int64_t* computed) {
-  Sim sim;
-  sim.g = h->g;
+// final state and exactly-once checks shared by both replays
+void final_checks(Sim& sim) {
   const Geom& g = sim.g;
-  sim.n_sub = nsteps * g.S;
-  if ((double)(sim.n_sub + 1) * (double)g.N > 4e8) {
-    h->err = "schedule check too large (n_sub * N > 4e8)";
-    return SWEPT_EINVAL;
-  }
-  sim.u.resize((size_t)g.C * g.N);
-  for (int c = 0; c < g.C; ++c)
-    for (int64_t x = 0; x < g.N; ++x) sim.u[(size_t)(c * g.N + x)] = Tag{x, 0};
-  for (int b = 0; b < 2; ++b) {
-    sim.e[b].assign((size_t)g.nt * g.E, Tag{});
-    sim.ae[b].assign((size_t)g.nt * g.E, Access{});
-  }
-  sim.au.assign((size_t)g.C * g.N, Access{});
-  sim.count.assign((size_t)(sim.n_sub + 1) * g.N, 0);
-  const int64_t q = sim.n_sub / g.h;
-  for_each_launch(g, sim.n_sub, [&](int kind, int odd, int mode, int hh, int64_t pass) {
-    ++sim.stamp;
-    // absolute tier of local tier 0 of this launch
-    const int64_t base = pass >= 0 ? (kind == 0 ? 0 : (pass - 1) * (int64_t)g.h) : q * (int64_t)g.h;
-    for (int64_t b = 0; b < g.nt && sim.err.empty(); ++b) {
-      if (kind == 0) {
-        const int out = pass >= 0 ? (int)(pass & 1) : 0;
-        HostCtx cx(sim, b, base, 0, out);
-        run_up(cx, g, b, hh, mode == MODE_GAP);
-      } else {
-        const int in = pass >= 1 ? (int)((pass - 1) & 1) : 0;
-        const int out = pass >= 1 ? (int)(pass & 1) : 1;
-        HostCtx cx(sim, b, base, in, out);
-        run_diamond(cx, g, b, odd, mode, hh);
-      }
-    }
-  });
   if (sim.err.empty()) {
     for (int c = 0; c < g.C && sim.err.empty(); ++c)
       for (int64_t x = 0; x < g.N; ++x) {
@@ -231,6 +240,115 @@ swept_status check_schedule(swept_handle* h, int64_t nsteps, int64_t* computed) 
         }
       }
   }
+}
+
+void init_sim(Sim& sim, const Geom& g, int64_t n_sub) {
+  sim.g = g;
+  sim.n_sub = n_sub;
+  sim.u.resize((size_t)g.C * g.N);
+  for (int c = 0; c < g.C; ++c)
+    for (int64_t x = 0; x < g.N; ++x) sim.u[(size_t)(c * g.N + x)] = Tag{x, 0};
+  for (int b = 0; b < 2; ++b) {
+    sim.e[b].assign((size_t)g.nt * g.E, Tag{});
+    sim.ae[b].assign((size_t)g.nt * g.E, Access{});
+  }
+  sim.au.assign((size_t)g.C * g.N, Access{});
+  sim.count.assign((size_t)(n_sub + 1) * g.N, 0);
+}
+
+// The persistent kernel's item queue (k_swept_persist), in queue order, which
+// is one order its waits allow; races are judged on the waits alone.
+swept_status check_persistent(swept_handle* h, int64_t nsteps, int64_t* computed) {
+  Sim sim;
+  const Geom& g0 = h->g;
+  init_sim(sim, g0, nsteps * g0.S);
+  const Geom& g = sim.g;
+  const int64_t q = sim.n_sub / g.h;
+  const int rem = (int)(sim.n_sub % g.h);
+  const int main_passes = q > 0 ? (int)q + 1 : 0;
+  const int64_t layers = main_passes + (rem > 0 ? 2 : 0);
+  const int64_t items = layers * g.nt;
+  if (items > 8192) {
+    h->err = "persistent schedule check too large (more than 8192 items)";
+    return SWEPT_EINVAL;
+  }
+  sim.hb_mode = true;
+  const size_t words = (size_t)((items + 63) / 64);
+  sim.anc.assign((size_t)items, std::vector<uint64_t>(words, 0));
+  sim.hb[BUF_U].assign((size_t)g.C * g.N, HbLoc{});
+  sim.hb[BUF_E0].assign((size_t)g.nt * g.E, HbLoc{});
+  sim.hb[BUF_E1].assign((size_t)g.nt * g.E, HbLoc{});
+  for (int64_t it = 0; it < items && sim.err.empty(); ++it) {
+    const int kp = (int)(it / g.nt);
+    const int64_t b = it - (int64_t)kp * g.nt;
+    int64_t dep_tile[3];
+    int dep_need[3];
+    const int ndep = persist_deps(g, sim.n_sub, kp, b, dep_tile, dep_need);
+    for (int i = 0; i < ndep; ++i) {
+      const int64_t d = (int64_t)dep_need[i] * g.nt + dep_tile[i];
+      if (d < 0 || d >= it) {
+        sim.fail("persistent item waits for an item that is not earlier in the queue");
+        break;
+      }
+      auto& a = sim.anc[(size_t)it];
+      const auto& ad = sim.anc[(size_t)d];
+      for (size_t w = 0; w < words; ++w) a[w] |= ad[w];
+      a[(size_t)(d >> 6)] |= 1ull << (d & 63);
+    }
+    if (!sim.err.empty()) break;
+    if (kp < main_passes) {
+      if (kp == 0) {
+        HostCtx cx(sim, it, 0, 0, 0);
+        run_up(cx, g, b, g.h, false);
+      } else {
+        HostCtx cx(sim, it, (int64_t)(kp - 1) * g.h, (kp - 1) & 1, kp & 1);
+        run_diamond(cx, g, b, kp & 1, kp == q ? MODE_DOWN : MODE_DIAMOND, g.h);
+      }
+    } else if (kp == main_passes) {
+      HostCtx cx(sim, it, q * g.h, 0, 0);
+      run_up(cx, g, b, rem, true);
+    } else {
+      HostCtx cx(sim, it, q * g.h, 0, 1);
+      run_diamond(cx, g, b, 1, MODE_GAP, rem);
+    }
+  }
+  final_checks(sim);
+  if (computed) *computed = sim.computed;
+  if (!sim.err.empty()) {
+    h->err = sim.err;
+    return SWEPT_EDEVICE;
+  }
+  return SWEPT_OK;
+}
+
+swept_status check_schedule(swept_handle* h, int64_t nsteps, int64_t* computed) {
+  if ((double)(nsteps * h->g.S + 1) * (double)h->g.N > 4e8) {
+    h->err = "schedule check too large (n_sub * N > 4e8)";
+    return SWEPT_EINVAL;
+  }
+  if (h->persistent) return check_persistent(h, nsteps, computed);
+  Sim sim;
+  init_sim(sim, h->g, nsteps * h->g.S);
+  const Geom& g = sim.g;
+  const int64_t q = sim.n_sub / g.h;
+  for_each_launch(g, sim.n_sub, [&](int kind, int odd, int mode, int hh, int64_t pass) {
+    ++sim.stamp;
+    // absolute tier of local tier 0 of this launch
+    const int64_t base = pass >= 0 ? (kind == 0 ? 0 : (pass - 1) * (int64_t)g.h) : q * (int64_t)g.h;
+    for (int64_t b = 0; b < g.nt && sim.err.empty(); ++b) {
+      if (kind == 0) {
+        const int out = pass >= 0 ? (int)(pass & 1) : 0;
+        HostCtx cx(sim, b, base, 0, out);
+        run_up(cx, g, b, hh, mode == MODE_GAP);
+      } else {
+        const int in = pass >= 1 ? (int)((pass - 1) & 1) : 0;
+        const int out = pass >= 1 ? (int)(pass & 1) : 1;
+        HostCtx cx(sim, b, base, in, out);
+        run_diamond(cx, g, b, odd, mode, hh);
+      }
+    }
+  });
+  final_checks(sim);
   if (computed) *computed = sim.computed;
   if (!sim.err.empty()) {
     h->err = sim.err;

@@ -578,16 +578,10 @@ __global__ void __launch_bounds__(P > 0 ? 32 : 1024, P > 0 ? 16 : 1) k_swept_per
     const int64_t b = item - (int64_t)kp * g.nt;
     if (threadIdx.x == 0) {
       bool ok = *(volatile int*)ctl.error == 0;
-      if (ok && kp < main_passes && kp > 0) {
-        const int odd = kp & 1;
-        ok = persist_wait(ctl.done + left_tile(g, odd, b), kp - 1, ctl) &&
-             persist_wait(ctl.done + right_tile(g, odd, b), kp - 1, ctl);
-      } else if (ok && kp == main_passes && q > 0) {
-        ok = persist_wait(ctl.done + (b + g.nt - 1) % g.nt, q, ctl) && persist_wait(ctl.done + b, q, ctl) &&
-             persist_wait(ctl.done + (b + 1) % g.nt, q, ctl);
-      } else if (ok && kp == main_passes + 1) {
-        ok = persist_wait(ctl.done + b, main_passes, ctl) && persist_wait(ctl.done + (b + 1) % g.nt, main_passes, ctl);
-      }
+      int64_t dep_tile[3];
+      int dep_need[3];
+      const int ndep = persist_deps(g, n_sub, kp, b, dep_tile, dep_need);
+      for (int i = 0; ok && i < ndep; ++i) ok = persist_wait(ctl.done + dep_tile[i], dep_need[i], ctl);
       if (!ok) atomicCAS(ctl.error, 0, 4);
       s_ok = ok;
       __threadfence();

@@ -110,6 +110,40 @@ SW_HD void run_diamond(Cx& cx, const Geom& g_in, int64_t b, int odd, int mode, i
   }
 }
 
+// The persistent form of the launch sequence below: item (layer kp, tile b),
+// item = kp * nt + b, runs launch kp's work for block b.  Before it runs it
+// waits until each tile tile[i] has completed layer need[i] (a tile's layers
+// complete in order, each one waiting for the tile's previous layer); this
+// returns how many such inputs the item has (0..3).  The zig-zag makes a
+// diamond depend on the two tiles it reads; the remainder trapezoid reads the
+// state the down-triangle wrote over its tile (tiles b-1, b, b+1 cover every
+// case); the gap pass reads the edges of the two trapezoids beside it.
+SW_HD int persist_deps(const Geom& g, int64_t n_sub, int kp, int64_t b, int64_t* tile, int* need) {
+  const int64_t q = n_sub / g.h;
+  const int rem = (int)(n_sub % g.h);
+  const int main_passes = q > 0 ? (int)q + 1 : 0;
+  if (kp > 0 && kp < main_passes) {
+    tile[0] = left_tile(g, kp & 1, b);
+    tile[1] = right_tile(g, kp & 1, b);
+    need[0] = need[1] = kp - 1;
+    return 2;
+  }
+  if (kp == main_passes && q > 0 && rem > 0) {
+    tile[0] = (b + g.nt - 1) % g.nt;
+    tile[1] = b;
+    tile[2] = (b + 1) % g.nt;
+    need[0] = need[1] = need[2] = (int)q;
+    return 3;
+  }
+  if (kp == main_passes + 1 && rem > 0) {
+    tile[0] = b;
+    tile[1] = (b + 1) % g.nt;
+    need[0] = need[1] = main_passes;
+    return 2;
+  }
+  return 0;
+}
+
 // The launch sequence for n_sub sub-timesteps: q = n_sub / h full passes
 // (up, q-1 diamonds, down) and, for rem = n_sub % h, an up-trapezoid and a
 // gap pass.  `emit(kind, odd, mode, hh, pass)` is called once per launch:

@@ -273,3 +273,31 @@ def test_set_option_rejects_invalid(S, option, value):
     assert S.swept_set_option(h.value, S.SWEPT_OPT_SPIN_LIMIT, 5000) == S.SWEPT_OK
     assert S.swept_set_option(h.value, S.SWEPT_OPT_START_ITEM, 3) == S.SWEPT_OK
     S.swept_free(h.value)
+
+
+def test_persistent_schedule_replay(S):
+    """For a persistent handle swept_check_schedule replays the persistent kernel's
+    item queue and checks the happens-before order its waits create (every read
+    after its writer; every overwrite after the previous writer and its readers),
+    besides the value flow.  Seeded sweep over schemes, boundaries, tile counts and
+    step counts (full passes, remainders, remainder only)."""
+    import numpy as np
+
+    g = np.random.default_rng(1208)
+    for _ in range(40):
+        scheme = int(g.integers(0, 3))
+        R = 1 if scheme == S.HEAT else 2
+        W = 4 * R * int(g.integers(1, 6))
+        nt = int(g.integers(2, 9))
+        bc = 0 if scheme == S.KS else int(g.integers(0, 2))
+        S_ = 1 if scheme == S.HEAT else 2
+        h = W // (2 * R)
+        nsteps = int(g.choice([1, max(1, h // S_), int(g.integers(1, 5 * h))]))
+        c = cfg(S, scheme=scheme, n=nt * W, tile_w=W, bc=bc, param0=1.4 if scheme == S.EULER else 1.0, persistent=1)
+        hh = ctypes.c_void_p()
+        assert S.swept_init(ctypes.byref(c), ctypes.byref(hh)) == S.SWEPT_OK
+        n = ctypes.c_int64()
+        st = S.swept_check_schedule(hh.value, nsteps, ctypes.byref(n))
+        assert st == S.SWEPT_OK, S.last_error(hh.value)
+        assert n.value == nt * W * nsteps * S_
+        S.swept_free(hh.value)
