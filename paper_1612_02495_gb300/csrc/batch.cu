@@ -138,24 +138,14 @@ __device__ __forceinline__ bool wait_ge(const int* flag, int need, uint32_t limi
 
 // thread 0: wait for the item's inputs; false on timeout
 __device__ bool wait_inputs(const BatchDev& d, const BatchProb& p, int k, int64_t b) {
+  // the single-problem persistent kernel's rule (persist_deps), per problem
   const int* done = d.done + p.t0;
-  const int main_passes = p.q > 0 ? p.q + 1 : 0;
-  if (k < main_passes) {
-    if (k == 0) return true;
-    const Geom g = geom_of(p);
-    const int odd = k & 1;
-    return wait_ge(done + left_tile(g, odd, b), k - 1, d.spin_limit, d.error) &&
-           wait_ge(done + right_tile(g, odd, b), k - 1, d.spin_limit, d.error);
-  }
-  const int r = k - main_passes;  // 0: remainder trapezoid, 1: gap pass
-  if (r == 0) {
-    if (p.q == 0) return true;
-    const int64_t bl = (b + p.nt - 1) % p.nt, br = (b + 1) % p.nt;
-    return wait_ge(done + bl, p.q, d.spin_limit, d.error) && wait_ge(done + b, p.q, d.spin_limit, d.error) &&
-           wait_ge(done + br, p.q, d.spin_limit, d.error);
-  }
-  const int kt = main_passes;
-  return wait_ge(done + b, kt, d.spin_limit, d.error) && wait_ge(done + (b + 1) % p.nt, kt, d.spin_limit, d.error);
+  int64_t tile[3];
+  int need[3];
+  const int n = persist_deps(geom_of(p), (int64_t)p.q * p.h + p.rem, k, b, tile, need);
+  for (int i = 0; i < n; ++i)
+    if (!wait_ge(done + tile[i], need[i], d.spin_limit, d.error)) return false;
+  return true;
 }
 
 template <typename T, class Op>
