@@ -156,13 +156,14 @@ def solver_from_plan(scheme, dtype, n, dx, dt, param0, plan, bc=S.BC_PERIODIC):
                     warp_tiles=plan.get("warp_tiles", 0))
 
 
-def tune_2d(dtype, nx, ny, probe_steps=200, tiles=(16, 32, 64, 128), threads=(256, 512, 1024), cache=DEFAULT_CACHE,
-            refresh=False, reps=2):
-    """Best (tile_w, threads) for swept2d_step_n on an nx x ny 2D heat problem."""
+def tune_2d(dtype, nx, ny, probe_steps=200, tiles=(16, 32, 64, 128), threads=(256, 512, 1024), modes=(0, 1),
+            cache=DEFAULT_CACHE, refresh=False, reps=2):
+    """Best (tile_w, threads, persistent) for swept2d_step_n on an nx x ny 2D heat
+    problem; modes: 0 one launch per pass, 1 the persistent queue kernel."""
     import torch
 
     table = _load(cache) if cache else {}
-    key = "2d/%s/%d/%d/%d/%d" % (_device_key(), dtype, nx, ny, probe_steps)
+    key = "2d2/%s/%d/%d/%d/%d/%s" % (_device_key(), dtype, nx, ny, probe_steps, "".join(str(m) for m in modes))
     if not refresh and key in table:
         return table[key]
     npd = np.float64 if dtype == S.F64 else np.float32
@@ -171,15 +172,17 @@ def tune_2d(dtype, nx, ny, probe_steps=200, tiles=(16, 32, 64, 128), threads=(25
     best = None
     for W in tiles:
         for t in threads:
-            try:
-                sol = S.Solver2D(dtype, nx, ny, p["dx"], p["dt"], p["alpha"], tile_w=W, threads=t)
-            except S.SweptError:
-                continue  # tile not legal for this grid or dtype
-            u = d0.clone()
-            ms = _time(lambda: sol.step(u, probe_steps), reps)
-            sol.close()
-            if best is None or ms < best["ms"]:
-                best = {"tile_w": W, "threads": t, "ms": ms, "probe_steps": probe_steps}
+            for m in modes:
+                try:
+                    sol = S.Solver2D(dtype, nx, ny, p["dx"], p["dt"], p["alpha"], tile_w=W, threads=t, persistent=m)
+                except S.SweptError:
+                    continue  # tile not legal for this grid or dtype
+                u = d0.clone()
+                ms = _time(lambda: sol.step(u, probe_steps), reps)
+                sol.sync_status()
+                sol.close()
+                if best is None or ms < best["ms"]:
+                    best = {"tile_w": W, "threads": t, "persistent": m, "ms": ms, "probe_steps": probe_steps}
     if cache:
         table = _load(cache)
         table[key] = best

@@ -3,6 +3,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <functional>
 #include <map>
 #include <new>
@@ -23,9 +24,15 @@ struct swept2d_handle {
   int device = -1;
   int value_bytes = 8;
   double fo = 0.0;  // alpha dt / dx^2, in double
+  bool persistent = false;
+  int persist_blocks = 0;  // resident blocks of the persistent kernel (0: not yet known)
+  int sm_count = 0;
+  uint32_t spin_limit = 1u << 24;
+  int64_t start_item = 0;
+  int64_t check_drop_wait = -1;  // replay only: an item whose last wait is dropped
   char* ws = nullptr;
   size_t ws_bytes = 0, ws_bound = 0;
-  size_t off_s0 = 0, off_s1 = 0, off_b = 0, off_tmp = 0, off_status = 0;
+  size_t off_s0 = 0, off_s1 = 0, off_b = 0, off_b1 = 0, off_tmp = 0, off_status = 0, off_persist = 0;
   cudaStream_t cap = nullptr;
   std::map<std::string, cudaGraphExec_t> graphs;
   std::string err;
@@ -33,7 +40,8 @@ struct swept2d_handle {
 
 namespace swept2d {
 // symbolic replay of the 2D launch sequence (check2d.cpp)
-bool check_schedule2d(const Geom2& g, int64_t nsteps, int64_t* computed, std::string* err);
+bool check_schedule2d(const Geom2& g, int64_t nsteps, bool persistent, int64_t drop_wait, int64_t* computed,
+                      std::string* err);
 }  // namespace swept2d
 
 namespace {
@@ -77,6 +85,8 @@ cudaError_t prepare_t(size_t smem) {
     e = cudaFuncSetAttribute(swept2d::k_bridge2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(swept2d::k_octa2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(swept2d::k_persist2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return e;
 }
 
@@ -141,6 +151,42 @@ cudaError_t issue_swept_t(swept2d_handle* h, T* u, int64_t n, int64_t from, int6
   return err;
 }
 
+// the persistent form: counters reset, one launch over the whole queue, the
+// error word latched into the status word
+template <typename T>
+cudaError_t issue_persist_t(swept2d_handle* h, T* u, int64_t n, cudaStream_t s) {
+  const Geom2& g = h->g;
+  const size_t T_ = (size_t)(g.ntx * g.nty);
+  char* pc = h->ws + h->off_persist;
+  int* tile_done = (int*)pc;
+  int* bridge_done = tile_done + T_;
+  char* ctl = pc + align_up(3 * T_ * sizeof(int));
+  cudaError_t e = cudaMemsetAsync(pc, 0xFF, 3 * T_ * sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, 16, s);
+  if (e != cudaSuccess) return e;
+  swept2d::Persist2Ctl c{tile_done, bridge_done, (unsigned long long*)ctl, (int*)(ctl + 8), h->spin_limit,
+                         h->start_item};
+  const int64_t items = swept2d::persist2d_items(g, n);
+  const unsigned blocks = (unsigned)std::min<int64_t>(items, h->persist_blocks);
+  swept2d::k_persist2d<T><<<blocks, h->threads, h->smem, s>>>(
+      g, consts<T>(h), u, (T*)(h->ws + h->off_s0), (T*)(h->ws + h->off_s1), (T*)(h->ws + h->off_b),
+      (T*)(h->ws + h->off_b1), n, c);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    swept2d::k_latch_error2d<<<1, 1, 0, s>>>((const int*)(ctl + 8), (int*)(h->ws + h->off_status));
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+template <typename T>
+int persist_blocks_per_sm_t(const swept2d_handle* h) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, swept2d::k_persist2d<T>, h->threads, h->smem) != cudaSuccess)
+    return 0;
+  return n;
+}
+
 cudaError_t issue_swept(swept2d_handle* h, void* u, int64_t n, int64_t from, int64_t to, cudaStream_t s) {
   return h->value_bytes == 8 ? issue_swept_t<double>(h, (double*)u, n, from, to, s)
                              : issue_swept_t<float>(h, (float*)u, n, from, to, s);
@@ -186,10 +232,14 @@ swept_status swept2d_init(const swept2d_config* cfg, swept2d_handle** out) {
   if (W <= 0 || !tile_ok(cfg->nx, cfg->ny, W, cfg->dtype)) return SWEPT_EINVAL;
   const int th = cfg->threads > 0 ? cfg->threads : 256;
   if (th < 32 || th > 1024 || th % 32 != 0) return SWEPT_EINVAL;
+  if (cfg->persistent != 0 && cfg->persistent != 1) return SWEPT_EINVAL;
+  for (int i = 0; i < 3; ++i)
+    if (cfg->reserved[i] != 0) return SWEPT_EINVAL;
   swept2d_handle* h = new (std::nothrow) swept2d_handle();
   if (!h) return SWEPT_EINVAL;
   h->cfg = *cfg;
   h->threads = th;
+  h->persistent = cfg->persistent == 1;
   h->value_bytes = cfg->dtype == SWEPT_F64 ? 8 : 4;
   h->fo = cfg->alpha * cfg->dt / (cfg->dx * cfg->dx);
   Geom2& g = h->g;
@@ -213,16 +263,24 @@ swept_status swept2d_init(const swept2d_config* cfg, swept2d_handle** out) {
   }
   const size_t vb = (size_t)h->value_bytes;
   const size_t strips = align_up((size_t)(g.ntx * g.nty * g.Es) * vb);
+  const size_t bands = align_up((size_t)(2 * g.ntx * g.nty * g.Eb) * vb);
   h->off_s0 = 0;
   h->off_s1 = strips;
   h->off_b = 2 * strips;
-  h->off_tmp = h->off_b + align_up((size_t)(2 * g.ntx * g.nty * g.Eb) * vb);
+  // the persistent kernel overlaps half cycles, so it double-buffers the bands too
+  h->off_b1 = h->off_b + bands;
+  h->off_tmp = h->off_b1 + (h->persistent ? bands : 0);
   h->off_status = h->off_tmp + align_up((size_t)(g.nx * g.ny) * vb);
-  h->ws_bytes = h->off_status + kAlign;
+  h->off_persist = h->off_status + kAlign;
+  const size_t T_ = (size_t)(g.ntx * g.nty);
+  h->ws_bytes = h->off_persist + (h->persistent ? align_up(3 * T_ * sizeof(int)) + kAlign : 0);
   int dev = -1;
   if (cudaGetDevice(&dev) == cudaSuccess) {
     int n = 0;
-    if (cudaGetDeviceCount(&n) == cudaSuccess && n > 0) h->device = dev;
+    if (cudaGetDeviceCount(&n) == cudaSuccess && n > 0) {
+      h->device = dev;
+      cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    }
   }
   cudaGetLastError();  // clear a no-device error
   *out = h;
@@ -245,6 +303,8 @@ swept_status swept2d_bind_workspace(swept2d_handle* h, void* ws_dev, size_t byte
   drop_graphs(h);
   h->ws = (char*)ws_dev;
   h->ws_bound = bytes;
+  cudaError_t e = cudaMemset(h->ws + h->off_status, 0, kAlign);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemset(status)");
   return SWEPT_OK;
 }
 
@@ -254,6 +314,18 @@ swept_status swept2d_step_n(swept2d_handle* h, void* u_dev, int64_t nsteps, void
   if (st != SWEPT_OK || nsteps == 0) return st;
   const cudaStream_t s = (cudaStream_t)stream;
   const Geom2& g = h->g;
+  if (h->persistent) {
+    if (nsteps / g.h + 1 > INT32_MAX) return fail(h, SWEPT_EINVAL, "nsteps too large for the persistent counters");
+    if (!h->persist_blocks) {
+      const int per_sm = h->value_bytes == 8 ? persist_blocks_per_sm_t<double>(h) : persist_blocks_per_sm_t<float>(h);
+      if (per_sm < 1 || h->sm_count < 1) return fail(h, SWEPT_EINVAL, "persistent kernel does not fit on an SM");
+      h->persist_blocks = per_sm * h->sm_count;
+    }
+    return run_graph(h, key_of("swept2d_persist", u_dev, nsteps), s, [&](cudaStream_t cs) {
+      return h->value_bytes == 8 ? issue_persist_t<double>(h, (double*)u_dev, nsteps, cs)
+                                 : issue_persist_t<float>(h, (float*)u_dev, nsteps, cs);
+    });
+  }
   const int64_t L = swept2d::launch_count2d(g, nsteps);
   const int64_t q = nsteps / g.h;
   const int64_t K = 256;  // half cycles per cached body graph (even: the body repeats with the tiling parity)
@@ -296,6 +368,7 @@ swept_status swept2d_get_plan(const swept2d_handle* h, swept2d_plan_info* out) {
   out->tile_w = h->g.W;
   out->threads = h->threads;
   out->half_cycle = h->g.h;
+  out->persistent = h->persistent ? 1 : 0;
   out->tiles_x = h->g.ntx;
   out->tiles_y = h->g.nty;
   out->smem_bytes = (int64_t)h->smem;
@@ -308,8 +381,42 @@ swept_status swept2d_check_schedule(swept2d_handle* h, int64_t nsteps, int64_t* 
   std::string err;
   if ((double)(nsteps + 1) * (double)(h->g.nx * h->g.ny) > 2e8)
     return fail(h, SWEPT_EINVAL, "schedule check too large ((nsteps + 1) * nx * ny > 2e8)");
-  if (!swept2d::check_schedule2d(h->g, nsteps, computed, &err)) return fail(h, SWEPT_EDEVICE, err);
+  if (h->persistent && swept2d::persist2d_items(h->g, nsteps) > 16384)
+    return fail(h, SWEPT_EINVAL, "persistent schedule check too large (more than 16384 items)");
+  if (!swept2d::check_schedule2d(h->g, nsteps, h->persistent, h->check_drop_wait, computed, &err))
+    return fail(h, SWEPT_EDEVICE, err);
   return SWEPT_OK;
+}
+
+swept_status swept2d_set_option(swept2d_handle* h, int32_t option, int64_t value) {
+  if (!h) return SWEPT_EINVAL;
+  if (option == SWEPT_OPT_SPIN_LIMIT) {
+    if (value < 1 || value > 0xffffffffLL) return fail(h, SWEPT_EINVAL, "spin limit outside [1, 2^32)");
+    h->spin_limit = (uint32_t)value;
+  } else if (option == SWEPT_OPT_START_ITEM) {
+    if (value < 0) return fail(h, SWEPT_EINVAL, "start item < 0");
+    h->start_item = value;
+  } else if (option == SWEPT2D_OPT_CHECK_DROP_WAIT) {
+    if (value < -1) return fail(h, SWEPT_EINVAL, "item < -1");
+    h->check_drop_wait = value;
+  } else {
+    return fail(h, SWEPT_EINVAL, "unknown option");
+  }
+  drop_graphs(h);  // captured persistent launches carry the options
+  return SWEPT_OK;
+}
+
+swept_status swept2d_sync_status(swept2d_handle* h, void* stream) {
+  if (!h) return SWEPT_EINVAL;
+  if (!h->ws) return fail(h, SWEPT_ENOWORKSPACE, "no workspace bound");
+  const cudaStream_t s = (cudaStream_t)stream;
+  int32_t word = 0;
+  cudaError_t e = cudaMemcpyAsync(&word, h->ws + h->off_status, sizeof word, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->off_status, 0, sizeof word, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "swept2d_sync_status");
+  if (word == 0) return SWEPT_OK;
+  return fail(h, word == SWEPT_ETIMEOUT ? SWEPT_ETIMEOUT : SWEPT_EDEVICE, "device-side error word set");
 }
 
 swept_status swept2d_last_error(const swept2d_handle* h, char* buf, size_t len) {

@@ -42,8 +42,10 @@ __device__ __forceinline__ void divmod_small(int a, int b, int& q, int& r) { div
 
 // Device context of one block: the two level rows of its (W + 2R)^2 window in
 // shared memory.  Loads and stores spread rows over warps and points of a row
-// over lanes; a level spreads its rectangle flat over the block.
-template <typename T>
+// over lanes; a level spreads its rectangle flat over the block.  COHERENT
+// (the persistent kernel): global loads go through L2 (ld.global.cg), since
+// other blocks of the same launch wrote what is read.
+template <typename T, bool COHERENT = false>
 struct Dev2Ctx {
   static constexpr int kR = 1;  // the 5-point heat stencil
   T* sm;
@@ -70,15 +72,21 @@ struct Dev2Ctx {
   __device__ __forceinline__ void sync() { __syncthreads(); }
   // the loop indices the phases split are < 1024 and the divisors <= 64
   __device__ __forceinline__ void divmod(int a, int b, int& q, int& r) const { divmod_small(a, b, q, r); }
+  __device__ __forceinline__ static T ld(const T* p) {
+    if constexpr (COHERENT)
+      return __ldcg(p);
+    else
+      return *p;
+  }
   __device__ __forceinline__ void load_u(int r, int lx, int ly, int64_t gx, int64_t gy) {
-    at(r, lx, ly) = u[gidx(gx, gy)];
+    at(r, lx, ly) = ld(u + gidx(gx, gy));
   }
   __device__ __forceinline__ void store_u(int r, int lx, int ly, int64_t gx, int64_t gy) {
     u[gidx(gx, gy)] = at(r, lx, ly);
   }
-  __device__ __forceinline__ void load_strip(int r, int lx, int ly, int64_t e) { at(r, lx, ly) = s_in[e]; }
+  __device__ __forceinline__ void load_strip(int r, int lx, int ly, int64_t e) { at(r, lx, ly) = ld(s_in + e); }
   __device__ __forceinline__ void store_strip(int r, int lx, int ly, int64_t e) { s_out[e] = at(r, lx, ly); }
-  __device__ __forceinline__ void load_band(int r, int lx, int ly, int64_t e) { at(r, lx, ly) = b_in[e]; }
+  __device__ __forceinline__ void load_band(int r, int lx, int ly, int64_t e) { at(r, lx, ly) = ld(b_in + e); }
   __device__ __forceinline__ void store_band(int r, int lx, int ly, int64_t e) { b_out[e] = at(r, lx, ly); }
   // level s on the local rectangle [x0, x1) x [y0, y1): row s & 1 from row
   // (s - 1) & 1.  The rectangle's points are spread flat over the block (point
@@ -155,6 +163,86 @@ __global__ void __launch_bounds__(1024) k_octa2d(Geom2 g, Heat2dK<T> k, T* u, co
   Dev2Ctx<T> cx{reinterpret_cast<T*>(smraw), g, k, u, s_in, s_out, b_in, nullptr};
   const int64_t b = blockIdx.x;
   run_octa(cx, g, b % g.ntx, b / g.ntx, odd, mode, hh);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent 2D swept kernel: the whole launch sequence as one queue of items
+// (persist2d_item), claimed in order by resident blocks through an atomic
+// counter.  Before running an item, thread 0 waits for the counters its inputs
+// come from (persist2d_deps); after it, the block publishes its own
+// (persist2d_signal).  An item only waits for items earlier in the queue, which
+// were claimed by blocks already resident, so the queue always drains.  A wait
+// that exceeds spin_limit polls sets the error word to SWEPT_ETIMEOUT (4) and
+// every block returns.
+// ---------------------------------------------------------------------------
+struct Persist2Ctl {
+  int* tile_done;             // T tile counters, -1 before the first pyramid
+  int* bridge_done;           // 2T bridge counters, -1 before the first bridge
+  unsigned long long* queue;  // next item
+  int* error;                 // SWEPT_ETIMEOUT (4) once a wait ran out
+  uint32_t spin_limit;
+  int64_t start_item;         // the first item claimed (0; > 0 only to exercise the timeout path)
+};
+
+__device__ __forceinline__ bool persist2d_wait(const int* flag, int need, const Persist2Ctl& c) {
+  for (uint32_t i = 0;; ++i) {
+    if (*(volatile const int*)flag >= need) return true;
+    if (i >= c.spin_limit || *(volatile const int*)c.error != 0) return false;
+    __nanosleep(128);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_persist2d(Geom2 g, Heat2dK<T> k, T* u, T* s0, T* s1, T* b0, T* b1,
+                                                     int64_t n, Persist2Ctl ctl) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int64_t s_item;
+  __shared__ int s_ok;
+  const int64_t total = persist2d_items(g, n);
+  T* S[2] = {s0, s1};
+  T* B[2] = {b0, b1};
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(ctl.queue, 1ULL) + ctl.start_item;
+    __syncthreads();
+    const int64_t item = s_item;
+    if (item >= total) break;
+    const PItem it = persist2d_item(g, n, item);
+    if (threadIdx.x == 0) {
+      bool ok = *(volatile int*)ctl.error == 0;
+      int counter[4];
+      int64_t index[4], need[4];
+      const int nd = persist2d_deps(g, n, it, counter, index, need);
+      for (int i = 0; ok && i < nd; ++i)
+        ok = persist2d_wait((counter[i] ? ctl.bridge_done : ctl.tile_done) + index[i], (int)need[i], ctl);
+      if (!ok) atomicCAS(ctl.error, 0, 4);
+      s_ok = ok;
+      __threadfence();
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    const PWork w = persist2d_work(g, n, it);
+    Dev2Ctx<T, true> cx{reinterpret_cast<T*>(smraw), g, k, u, S[w.s_in], S[w.s_out], B[w.b_in], B[w.b_out]};
+    const int64_t tx = it.idx % g.ntx, ty = it.idx / g.ntx;
+    if (it.kind == K_PYR)
+      run_pyr(cx, g, tx, ty, w.par, w.hh, w.mode == M2_GAP);
+    else if (it.kind == K_BRIDGE)
+      run_bridge(cx, g, it.idx, w.par, w.hh, w.mode == M2_GAP);
+    else
+      run_octa(cx, g, tx, ty, w.par, w.mode, w.hh);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int sc;
+      int64_t si, ss;
+      persist2d_signal(g, n, it, &sc, &si, &ss);
+      atomicExch((sc ? ctl.bridge_done : ctl.tile_done) + si, (int)ss);
+    }
+  }
+}
+
+// copies a device-side error word into the handle's status word (first error wins)
+static __global__ void k_latch_error2d(const int* err, int* status) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && *err != 0 && *status == 0) *status = *err;
 }
 
 // classic: one step of the whole grid, global memory in and out; periodic

@@ -298,6 +298,160 @@ inline void for_each_launch2d(const Geom2& g, int64_t n, F emit) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent form of the launch sequence: one queue of items run by a
+// persistent kernel whose blocks order themselves only through waits on
+// per-tile and per-bridge counters.  Queue order (T = tiles):
+//   PYR of cycle 0 (T items) | per half cycle c = 1..q: BRIDGE_c (2T), OCTA_c (T)
+//   | remainder: PYR (T), BRIDGE (2T), OCTA (T)
+// Counters: tile_done[t] = stage of the last finished PYR / OCTA of tile slot t
+// (PYR 0, OCTA_c c, remainder PYR q + 1); bridge_done[b] likewise for the
+// bridges (BRIDGE_c c, remainder q + 1).  Buffers: strips of cycle c in
+// S[c & 1]; bands of cycle c in B[c & 1]; the remainder uses S[q & 1] and
+// B[(q + 1) & 1].
+// ---------------------------------------------------------------------------
+struct PItem {
+  int kind;     // K_PYR, K_BRIDGE, K_OCTA
+  int64_t c;    // half cycle (PYR of cycle 0: 0); -1 for the remainder
+  int64_t idx;  // tile slot (PYR, OCTA) or bridge id (BRIDGE)
+};
+
+SW_HD int64_t persist2d_items(const Geom2& g, int64_t n) {
+  const int64_t T = g.ntx * g.nty, q = n / g.h;
+  return (q > 0 ? T + q * 3 * T : 0) + (n % g.h ? 4 * T : 0);
+}
+
+SW_HD PItem persist2d_item(const Geom2& g, int64_t n, int64_t item) {
+  const int64_t T = g.ntx * g.nty, q = n / g.h;
+  const int64_t main_items = q > 0 ? T + q * 3 * T : 0;
+  PItem it;
+  if (item < main_items) {
+    if (item < T) {
+      it.kind = K_PYR;
+      it.c = 0;
+      it.idx = item;
+      return it;
+    }
+    const int64_t rel = item - T;
+    it.c = rel / (3 * T) + 1;
+    const int64_t r = rel - (it.c - 1) * 3 * T;
+    if (r < 2 * T) {
+      it.kind = K_BRIDGE;
+      it.idx = r;
+    } else {
+      it.kind = K_OCTA;
+      it.idx = r - 2 * T;
+    }
+    return it;
+  }
+  const int64_t rel = item - main_items;
+  it.c = -1;
+  if (rel < T) {
+    it.kind = K_PYR;
+    it.idx = rel;
+  } else if (rel < 3 * T) {
+    it.kind = K_BRIDGE;
+    it.idx = rel - T;
+  } else {
+    it.kind = K_OCTA;
+    it.idx = rel - 3 * T;
+  }
+  return it;
+}
+
+// The waits of an item: up to four (counter, index, stage) triples; counter 0
+// is tile_done, 1 is bridge_done.  Returns their number.
+SW_HD int persist2d_deps(const Geom2& g, int64_t n, const PItem& it, int* counter, int64_t* index, int64_t* need) {
+  const int64_t q = n / g.h;
+  const int64_t tx = it.idx % g.ntx, ty = (it.idx / g.ntx) % g.nty;
+  if (it.c == 0) return 0;  // the first pyramid
+  if (it.c > 0 || it.kind != K_PYR) {
+    const int64_t c = it.c > 0 ? it.c : q + 1;  // remainder bridges and corners are stage q + 1
+    if (it.kind == K_BRIDGE) {
+      // its two pyramids of the previous tiling: the last OCTA (or PYR) of those slots
+      const bool ydir = it.idx >= g.ntx * g.nty;
+      const int64_t t = ydir ? it.idx - g.ntx * g.nty : it.idx;
+      const int64_t bx = t % g.ntx, by = t / g.ntx;
+      counter[0] = counter[1] = 0;
+      index[0] = tile_id(g, bx, by);
+      index[1] = ydir ? tile_id(g, bx, by + 1) : tile_id(g, bx + 1, by);
+      need[0] = need[1] = it.c > 0 ? c - 1 : q + 1;  // the remainder waits for the remainder pyramid
+      return 2;
+    }
+    // K_OCTA: the four bridges meeting at its corner (through them, the four tiles)
+    const int odd = it.c > 0 ? (int)(it.c & 1) : 1;
+    const int64_t lx_t = odd ? tx : tx - 1, rx_t = odd ? tx + 1 : tx;
+    const int64_t ly_t = odd ? ty : ty - 1, uy_t = odd ? ty + 1 : ty;
+    counter[0] = counter[1] = counter[2] = counter[3] = 1;
+    index[0] = xbridge_id(g, lx_t, uy_t);
+    index[1] = xbridge_id(g, lx_t, ly_t);
+    index[2] = ybridge_id(g, rx_t, ly_t);
+    index[3] = ybridge_id(g, lx_t, ly_t);
+    need[0] = need[1] = need[2] = need[3] = c;
+    return 4;
+  }
+  // remainder PYR of tile (tx, ty) of the unshifted tiling: the last full OCTA
+  // wrote the state over it from the (tx-1 .. tx) x (ty-1 .. ty) slots of its
+  // tiling (one slot when that tiling is unshifted); none when q = 0
+  if (q == 0) return 0;
+  for (int i = 0; i < 4; ++i) {
+    counter[i] = 0;
+    index[i] = tile_id(g, tx - (i & 1), ty - (i >> 1));
+    need[i] = q;
+  }
+  return 4;
+}
+
+// The counter an item sets when it finishes: (counter, index, stage) as in
+// persist2d_deps.  Every item sets one; nothing waits on the remainder OCTA's.
+SW_HD void persist2d_signal(const Geom2& g, int64_t n, const PItem& it, int* counter, int64_t* index,
+                            int64_t* stage) {
+  *counter = it.kind == K_BRIDGE ? 1 : 0;
+  *index = it.idx;
+  *stage = it.c >= 0 ? it.c : n / g.h + 1;
+}
+
+// What an item runs: buffers (strip in/out, band in/out), tiling parity
+// (PYR / BRIDGE) or produced tiling (OCTA), mode, levels and the absolute level
+// of its local level 0.  Shared by the persistent kernel and the replay.
+struct PWork {
+  int s_in, s_out, b_in, b_out, par, mode, hh;
+  int64_t base;
+};
+SW_HD PWork persist2d_work(const Geom2& g, int64_t n, const PItem& it) {
+  const int64_t q = n / g.h;
+  const int rem = (int)(n % g.h);
+  PWork w;
+  w.s_in = w.s_out = w.b_in = w.b_out = 0;
+  if (it.c >= 0) {
+    const int cp = (int)((it.c + 1) & 1), cc = (int)(it.c & 1);  // parities of c - 1 and c
+    w.hh = g.h;
+    w.base = it.c > 0 ? (it.c - 1) * (int64_t)g.h : 0;
+    w.mode = (it.kind == K_OCTA && it.c == q) ? M2_DOWN : M2_FULL;
+    if (it.kind == K_PYR) {
+      w.s_out = 0;
+      w.par = 0;
+    } else if (it.kind == K_BRIDGE) {
+      w.s_in = cp;
+      w.b_out = cc;
+      w.par = cp;
+    } else {
+      w.s_in = cp;
+      w.s_out = cc;
+      w.b_in = cc;
+      w.par = cc;
+    }
+  } else {
+    w.hh = rem;
+    w.base = q * (int64_t)g.h;
+    w.mode = M2_GAP;
+    w.s_in = w.s_out = (int)(q & 1);
+    w.b_in = w.b_out = (int)((q + 1) & 1);
+    w.par = it.kind == K_OCTA ? 1 : 0;
+  }
+  return w;
+}
+
 inline int64_t launch_count2d(const Geom2& g, int64_t n) {
   const int64_t q = n / g.h;
   return (q > 0 ? 1 + 2 * q : 0) + (n % g.h ? 3 : 0);

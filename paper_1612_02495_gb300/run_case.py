@@ -78,7 +78,8 @@ def main(argv=None):
 def run_heat2d(a, S, inputs, torch, npd, dt_code):
     """2D heat on an n x n grid (--n is the side): swept2d_step_n or classic2d_step_n."""
     p = inputs.heat2d_problem(nx=a.n, ny=a.n, dtype=npd)
-    sol = S.Solver2D(dt_code, a.n, a.n, p["dx"], p["dt"], p["alpha"], tile_w=a.tile, threads=a.threads)
+    sol = S.Solver2D(dt_code, a.n, a.n, p["dx"], p["dt"], p["alpha"], tile_w=a.tile, threads=a.threads,
+                     persistent=1 if a.persistent else 0)
     u_init = torch.from_numpy(p["u0"]).cuda()
     u = u_init.clone()
     run = sol.step if a.path == "swept" else sol.classic
@@ -93,6 +94,7 @@ def run_heat2d(a, S, inputs, torch, npd, dt_code):
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
+    sol.sync_status()
     ms = float(np.median(times))
     print(json.dumps({"scheme": "heat2d", "dtype": a.dtype, "n": a.n, "nsteps": a.nsteps, "path": a.path,
                       "plan": sol.plan, "ms": ms, "cell_updates_per_s": a.n * a.n * a.nsteps / (ms * 1e-3)}))

@@ -406,12 +406,13 @@ class Batch:
 class swept2d_config(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int32), ("bc", ctypes.c_int32), ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
                 ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("alpha", ctypes.c_double),
-                ("tile_w", ctypes.c_int32), ("threads", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("tile_w", ctypes.c_int32), ("threads", ctypes.c_int32), ("persistent", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class swept2d_plan_info(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("threads", ctypes.c_int32), ("half_cycle", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("tiles_x", ctypes.c_int64), ("tiles_y", ctypes.c_int64),
+                ("persistent", ctypes.c_int32), ("tiles_x", ctypes.c_int64), ("tiles_y", ctypes.c_int64),
                 ("smem_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64)]
 
 
@@ -423,14 +424,17 @@ classic2d_step_n = _sig("classic2d_step_n", [_H, _P, _I64, _P])
 swept2d_get_plan = _sig("swept2d_get_plan", [_H, ctypes.POINTER(swept2d_plan_info)])
 swept2d_check_schedule = _sig("swept2d_check_schedule", [_H, _I64, ctypes.POINTER(_I64)])
 swept2d_last_error = _sig("swept2d_last_error", [_H, ctypes.c_char_p, _SZ])
+swept2d_set_option = _sig("swept2d_set_option", [_H, ctypes.c_int32, _I64])
+swept2d_sync_status = _sig("swept2d_sync_status", [_H, _P])
+SWEPT2D_OPT_CHECK_DROP_WAIT = 16
 swept2d_free = _sig("swept2d_free", [_H], None)
 
 
-def make_config2d(dtype, nx, ny, dx, dt, alpha, tile_w=0, threads=0, bc=BC_PERIODIC):
+def make_config2d(dtype, nx, ny, dx, dt, alpha, tile_w=0, threads=0, bc=BC_PERIODIC, persistent=0):
     c = swept2d_config()
     c.dtype, c.bc, c.nx, c.ny = int(dtype), int(bc), int(nx), int(ny)
     c.dx, c.dt, c.alpha = float(dx), float(dt), float(alpha)
-    c.tile_w, c.threads = int(tile_w), int(threads)
+    c.tile_w, c.threads, c.persistent = int(tile_w), int(threads), int(persistent)
     return c
 
 
@@ -444,10 +448,10 @@ class Solver2D:
     """A 2D swept handle plus its workspace (a torch uint8 tensor on the current
     device).  States are contiguous CUDA tensors of shape (ny, nx)."""
 
-    def __init__(self, dtype, nx, ny, dx, dt, alpha, tile_w=0, threads=0, bc=BC_PERIODIC):
+    def __init__(self, dtype, nx, ny, dx, dt, alpha, tile_w=0, threads=0, bc=BC_PERIODIC, persistent=0):
         import torch
 
-        self.cfg = make_config2d(dtype, nx, ny, dx, dt, alpha, tile_w, threads, bc)
+        self.cfg = make_config2d(dtype, nx, ny, dx, dt, alpha, tile_w, threads, bc, persistent)
         h = _H()
         st = swept2d_init(ctypes.byref(self.cfg), ctypes.byref(h))
         if st != SWEPT_OK:
@@ -487,6 +491,14 @@ class Solver2D:
                     "classic2d_step_n")
         return u
 
+    def set_option(self, option, value):
+        """swept2d_set_option (SWEPT_OPT_SPIN_LIMIT, SWEPT_OPT_START_ITEM)."""
+        self._check(swept2d_set_option(self.h, int(option), int(value)), "swept2d_set_option")
+
+    def sync_status(self, stream=None):
+        """swept2d_sync_status: raises SweptError(SWEPT_ETIMEOUT) if a persistent wait ran out."""
+        self._check(swept2d_sync_status(self.h, _stream_ptr(stream)), "swept2d_sync_status")
+
     def close(self):
         if self.h:
             swept2d_free(self.h)
@@ -499,15 +511,20 @@ class Solver2D:
             pass
 
 
-def check_schedule2d(dtype, nx, ny, tile_w, nsteps, threads=0, bc=BC_PERIODIC):
-    """Host-only symbolic replay of the 2D launch sequence (no GPU): returns the
-    number of point updates, raises SweptError with the first violation."""
-    cfg = make_config2d(dtype, nx, ny, 1.0, 0.2, 1.0, tile_w, threads, bc)
+def check_schedule2d(dtype, nx, ny, tile_w, nsteps, threads=0, bc=BC_PERIODIC, persistent=0, drop_wait=-1):
+    """Host-only symbolic replay of the 2D launch sequence, or of the persistent
+    queue (no GPU): returns the number of point updates, raises SweptError with
+    the first violation.  drop_wait >= 0 drops the last wait of that queue item."""
+    cfg = make_config2d(dtype, nx, ny, 1.0, 0.2, 1.0, tile_w, threads, bc, persistent)
     h = _H()
     st = swept2d_init(ctypes.byref(cfg), ctypes.byref(h))
     if st != SWEPT_OK:
         raise SweptError(st, "swept2d_init rejected the configuration")
     try:
+        if drop_wait >= 0:
+            st = swept2d_set_option(h.value, SWEPT2D_OPT_CHECK_DROP_WAIT, int(drop_wait))
+            if st != SWEPT_OK:
+                raise SweptError(st, _err2d(h.value))
         n = _I64()
         st = swept2d_check_schedule(h.value, int(nsteps), ctypes.byref(n))
         if st != SWEPT_OK:
