@@ -44,11 +44,11 @@ FP64_KS_MIX_CEILING = 0.535e12
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_swept_diamond<double, KsOp> launch at
 # N = 2^20, tile 1024 (ncu, profiles/k_swept_diamond_ks_f64_n1048576.md); None once the kernel changes
 DIAMOND_TRAFFIC_BYTES = None
-# same for one k_swept_persist<double, KsOp> launch of the bench's tuned plan (tile 1024, 256 threads,
-# a whole 50,000-step solve): 10.36 MB read + 28.67 MB written (profiles/k_swept_persist_ks_f64_n1048576.md);
-# None once the kernel or the plan changes
-PERSIST_TRAFFIC_BYTES = 39030000
-PERSIST_TRAFFIC_TILE = 1024  # captured with 256 threads; the thread count moves no DRAM data (state once, edges in L2)
+# same for one k_swept_persist<double, KsOp> launch of the bench's tuned plan (tile 1024, 512 threads,
+# a whole 50,000-step solve): 11.88 MB read + 36.98 MB written (ncu, one pass; the command is in
+# profiles/launches_bench_ks_f64_n1048576.md); None once the kernel or the plan changes
+PERSIST_TRAFFIC_BYTES = 48860000
+PERSIST_TRAFFIC_PLAN = (1024, 512)  # (tile, threads) of that capture
 
 
 def peaks():
@@ -493,10 +493,11 @@ def main():
                     "pipe_frac": FP64_INSTR_PER_SUBSTEP * units / (ms * 1e-3) / FP64_INSTR_PEAK,
                     "frac_of_measured_mix_ceiling": FP64_INSTR_PER_SUBSTEP * units / (ms * 1e-3) / FP64_KS_MIX_CEILING,
                     "kernel_ms_avg": ms, "kernel_share": 1.0}
-        if plan["tile_w"] != PERSIST_TRAFFIC_TILE or plan.get("warp_tiles"):
-            roofline["traffic"] = None  # the ncu figure is for the tile-1024 shared-memory plan
+        if (plan["tile_w"], plan["threads"]) != PERSIST_TRAFFIC_PLAN or plan.get("warp_tiles"):
+            roofline["traffic"] = None  # the ncu figure is for another plan
         else:
-            roofline["traffic_note"] = "ncu capture of the tile-1024 persistent launch (256 threads), 50,000 steps"
+            roofline["traffic_note"] = "ncu capture of this plan's persistent launch (tile 1024, 512 threads), " \
+                                       "50,000 steps"
         roofline["frac"] = roofline["achieved"] / FP64_PEAK_TFLOPS
         launches_per_step = 2
     else:
