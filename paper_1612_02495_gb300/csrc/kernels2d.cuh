@@ -106,17 +106,17 @@ struct Dev2Ctx {
       divmod_small(t, w, rw, y, x);
       divmod_small(nt, w, rw, dy, dx);
       if (wx == swept::NO_WALL && wy == swept::NO_WALL) {
-        T* o = out + (y0 + y) * M + x0;
-        const T* c = in + (y0 + y) * M + x0;
+        // one 32-bit window offset per point: a step of nt points is dy rows
+        // and dx columns, plus a row when the column wraps
+        int off = (y0 + y) * M + x0 + x;
+        const int step = dy * M + dx, wrap = M - w;
         for (int i = t; i < n; i += nt) {
-          o[x] = heat2d_point<T>(c + x, M, k);
+          out[off] = heat2d_point<T>(in + off, M, k);
           x += dx;
-          o += dy * M;
-          c += dy * M;
+          off += step;
           if (x >= w) {
             x -= w;
-            o += M;
-            c += M;
+            off += wrap;
           }
         }
       } else {
