@@ -286,6 +286,29 @@ swept_status swept_get_plan(const swept_handle* h, swept_plan_info* out);
 enum { SWEPT_OPT_SPIN_LIMIT = 1, SWEPT_OPT_START_ITEM = 2 };
 swept_status swept_set_option(swept_handle* h, int32_t option, int64_t value);
 
+/*
+ * Debug build.  libswept_debug.so is the same library compiled with device-side
+ * index checks: every window position, tier range, edge / strip / band index,
+ * state coordinate, awaited counter and tape slot a kernel computes is checked
+ * before use.  A failing check skips the access and records the first failure
+ * (no trap).
+ *
+ * swept_debug_status: *enabled = 1 in the debug build, 0 otherwise.  In the
+ * debug build it then synchronizes the device, reads and clears every record:
+ * SWEPT_OK if no check failed since the last call, else SWEPT_EDEVICE with the
+ * first failure's check id (*check: 1 window, 2 edge, 3 level range, 4 state
+ * coordinate, 5 strip, 6 band, 7 counter, 8 tape slot, 9 probe) and index
+ * (*index).  SWEPT_ECUDA if the device cannot be read.  Pointers may be NULL.
+ *
+ * swept_debug_probe: exercises the recording path.  For i < n it copies
+ * buf[i] to buf[i] (device array of n doubles) behind a check of i < bound,
+ * 0 <= bound <= n, so the checks of i >= bound fail and skip a copy that would
+ * have been in range anyway.  Asynchronous on the stream; SWEPT_EINVAL for
+ * bad arguments.
+ */
+swept_status swept_debug_status(int32_t* enabled, int32_t* check, int64_t* index);
+swept_status swept_debug_probe(double* buf, int64_t n, int64_t bound, void* stream);
+
 /* Synchronize `stream`, then read and clear the device-side error word.
  * Returns SWEPT_OK, SWEPT_ETIMEOUT or SWEPT_EDEVICE. */
 swept_status swept_sync_status(swept_handle* h, void* stream);

@@ -1,7 +1,9 @@
 """Build libswept.so (the C-ABI CUDA library) in-tree for sm_103a.
 
 Each translation unit is compiled by nvcc in parallel and linked into
-paper_1612_02495_gb300/libswept.so.  Flags:
+paper_1612_02495_gb300/libswept.so.  build(debug=True) builds the same sources
+with -DSWEPT_DEBUG=1 (device-side index checks, csrc/debug_check.cuh) into
+libswept_debug.so, which the binding loads when SWEPT_DEBUG=1 is set.  Flags:
   -gencode arch=compute_103a,code=sm_103a   GB300 only
   --fmad=false, -ffp-contract=off           no multiply-add is fused unless the
                                             source spells out an fma intrinsic
@@ -18,6 +20,8 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libswept.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libswept_debug.so")
 
 SOURCES = ["api.cu", "impl_heat.cu", "impl_ks.cu", "impl_euler.cu", "check.cpp", "noalloc.cu", "batch.cu", "api2d.cu",
            "check2d.cpp"]
@@ -37,39 +41,41 @@ def _deps():
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "swept.h"), os.path.join(INCLUDE, "swept2d.h"), __file__]
 
 
-def _stale():
-    if not os.path.exists(LIB):
+def _stale(lib):
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def _compile(src):
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [_nvcc()] + ARCH + COMMON + ["-c", os.path.join(CSRC, src), "-o", obj]
+def _compile(src, debug=False):
+    obj = os.path.join(BUILD_DEBUG if debug else BUILD, os.path.splitext(src)[0] + ".o")
+    cmd = [_nvcc()] + ARCH + COMMON + (["-DSWEPT_DEBUG=1"] if debug else []) + ["-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, " ".join(cmd), r.stderr))
     return obj
 
 
-def build(force=False, verbose=False):
-    """Compile libswept.so if missing or older than its sources; return its path."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force=False, verbose=False, debug=False):
+    """Compile libswept.so (libswept_debug.so with debug=True) if missing or older
+    than its sources; return its path."""
+    lib = LIB_DEBUG if debug else LIB
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(BUILD_DEBUG if debug else BUILD, exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(_compile, SOURCES))
-    tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda src: _compile(src, debug), SOURCES))
+    tmp = lib + ".tmp"
     cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-Xcompiler", "-fPIC", "-ldl"]  # -ldl: NVTX tool loading
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
-        print("built", LIB)
-    return LIB
+        print("built", lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, debug="--debug" in sys.argv))

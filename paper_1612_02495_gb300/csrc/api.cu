@@ -6,6 +6,7 @@
 #include <functional>
 #include <new>
 #include <string>
+#include <vector>
 
 #include <algorithm>
 
@@ -656,6 +657,56 @@ swept_status swept_sync_status(swept_handle* h, void* stream) {
   if (e != cudaSuccess) return cuda_fail(h, e, "swept_sync_status");
   if (word == 0) return SWEPT_OK;
   return fail(h, word == SWEPT_ETIMEOUT ? SWEPT_ETIMEOUT : SWEPT_EDEVICE, "device-side error word set");
+}
+
+}  // extern "C"
+
+namespace swept {
+namespace dbg {
+namespace {
+std::vector<FetchFn>& fetchers() {
+  static std::vector<FetchFn> v;
+  return v;
+}
+__global__ void k_debug_probe(double* buf, int64_t n, int64_t bound) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (in_range(i, bound, PROBE)) buf[i] = buf[i];
+}
+}  // namespace
+void register_fetch(FetchFn f) { fetchers().push_back(f); }
+}  // namespace dbg
+}  // namespace swept
+
+extern "C" {
+
+swept_status swept_debug_status(int32_t* enabled, int32_t* check, int64_t* index) {
+  if (enabled) *enabled = SWEPT_DEBUG;
+  if (check) *check = 0;
+  if (index) *index = 0;
+  if (!SWEPT_DEBUG) return SWEPT_OK;
+  if (cudaDeviceSynchronize() != cudaSuccess) return SWEPT_ECUDA;
+  unsigned long long first = 0;
+  for (swept::dbg::FetchFn f : swept::dbg::fetchers()) {
+    unsigned long long w = 0;
+    if (f(&w) != cudaSuccess) return SWEPT_ECUDA;
+    if (!first) first = w;
+  }
+  if (!first) return SWEPT_OK;
+  if (check) *check = (int32_t)(first >> 48);
+  if (index) {
+    int64_t v = (int64_t)(first & 0xffffffffffffULL);
+    if (v & (1LL << 47)) v -= (1LL << 48);  // sign of the 48-bit field
+    *index = v;
+  }
+  return SWEPT_EDEVICE;
+}
+
+swept_status swept_debug_probe(double* buf, int64_t n, int64_t bound, void* stream) {
+  if (n < 0 || bound < 0 || bound > n || (n > 0 && !buf)) return SWEPT_EINVAL;
+  if (n == 0) return SWEPT_OK;
+  const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 1024);
+  swept::dbg::k_debug_probe<<<blocks, 256, 0, (cudaStream_t)stream>>>(buf, n, bound);
+  return cudaGetLastError() == cudaSuccess ? SWEPT_OK : SWEPT_ECUDA;
 }
 
 swept_status swept_set_option(swept_handle* h, int32_t option, int64_t value) {

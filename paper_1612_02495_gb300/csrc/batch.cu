@@ -28,6 +28,7 @@
 #include <string>
 #include <vector>
 
+#include "debug_check.cuh"
 #include "impl.h"
 #include "ops.cuh"
 #include "swept.h"
@@ -83,13 +84,21 @@ struct BatchCtx {
   __device__ __forceinline__ void sync() { __syncthreads(); }
   __device__ __forceinline__ T* row(int r, int c) { return sm + (r * Op::C + c) * g.M; }
   __device__ __forceinline__ void load_u(int r, int c, int j, int64_t x) {
-    row(r, c)[j] = __ldcg(u + c * g.N + wrap_n(x, g.N));
+    if (dbg::win(g.M, r, c, kC, j)) row(r, c)[j] = __ldcg(u + c * g.N + wrap_n(x, g.N));
   }
-  __device__ __forceinline__ void store_u(int r, int c, int j, int64_t x) { u[c * g.N + wrap_n(x, g.N)] = row(r, c)[j]; }
-  __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) { row(r, c)[j] = __ldcg(e_in + e); }
-  __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) { e_out[e] = row(r, c)[j]; }
+  __device__ __forceinline__ void store_u(int r, int c, int j, int64_t x) {
+    if (dbg::win(g.M, r, c, kC, j)) u[c * g.N + wrap_n(x, g.N)] = row(r, c)[j];
+  }
+  __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) {
+    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, g.nt * g.E, dbg::EDGE)) row(r, c)[j] = __ldcg(e_in + e);
+  }
+  __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) {
+    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, g.nt * g.E, dbg::EDGE)) e_out[e] = row(r, c)[j];
+  }
   __device__ __forceinline__ void level(int s, int, int lo, int hi, int64_t, int wall) {
-    if (stage_c<Op>(s) == 0)
+    if (!dbg::level(g.M, lo, hi, kR))
+      ;
+    else if (stage_c<Op>(s) == 0)
       scalar_tier<0>(lo, hi, s & 1, wall);
     else
       scalar_tier<1>(lo, hi, s & 1, wall);
@@ -144,7 +153,8 @@ __device__ bool wait_inputs(const BatchDev& d, const BatchProb& p, int k, int64_
   int need[3];
   const int n = persist_deps(geom_of(p), (int64_t)p.q * p.h + p.rem, k, b, tile, need);
   for (int i = 0; i < n; ++i)
-    if (!wait_ge(done + tile[i], need[i], d.spin_limit, d.error)) return false;
+    if (!dbg::in_range(tile[i], p.nt, dbg::COUNTER) || !wait_ge(done + tile[i], need[i], d.spin_limit, d.error))
+      return false;
   return true;
 }
 

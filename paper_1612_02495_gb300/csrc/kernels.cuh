@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "debug_check.cuh"
 #include "ops.cuh"
 #include "swept_geom.cuh"
 #include "swept_phases.cuh"
@@ -347,15 +348,19 @@ struct DevCtx {
   __device__ __forceinline__ void sync() { __syncthreads(); }
   __device__ __forceinline__ T* row(int r, int c) { return sm + (r * Op::C + c) * g.M; }
   __device__ __forceinline__ void load_u(int r, int c, int j, int64_t x) {
-    row(r, c)[j] = u_in[c * g.N + wrap_n(x, g.N)];
+    if (dbg::win(g.M, r, c, kC, j)) row(r, c)[j] = u_in[c * g.N + wrap_n(x, g.N)];
   }
   __device__ __forceinline__ void store_u(int r, int c, int j, int64_t x) {
-    u_out[c * g.N + wrap_n(x, g.N)] = row(r, c)[j];
+    if (dbg::win(g.M, r, c, kC, j)) u_out[c * g.N + wrap_n(x, g.N)] = row(r, c)[j];
   }
-  __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) { row(r, c)[j] = e_in[e]; }
-  __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) { e_out[e] = row(r, c)[j]; }
+  __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) {
+    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, g.nt * g.E, dbg::EDGE)) row(r, c)[j] = e_in[e];
+  }
+  __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) {
+    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, g.nt * g.E, dbg::EDGE)) e_out[e] = row(r, c)[j];
+  }
   __device__ __forceinline__ void level(int s, int base, int lo, int hi, int64_t origin, int wall) {
-    LevelImpl<T, Op>::run(sm, g.M, stage_c<Op>(s), s & 1, lo, hi, wall, g.chunk, k);
+    if (dbg::level(g.M, lo, hi, kR)) LevelImpl<T, Op>::run(sm, g.M, stage_c<Op>(s), s & 1, lo, hi, wall, g.chunk, k);
     if (TAPE) {
       // each thread stores the values it computed itself, so no barrier is needed first
       const int64_t slot = tape.base + base + s - tape.tier0;
@@ -436,6 +441,7 @@ struct RegCtx : Base {
   }
   // tier s on [lo, hi): into row s&1 from row (s-1)&1; stage (s-1) mod S
   __device__ __forceinline__ void level(int s, int, int lo, int hi, int64_t, int wall) {
+    if (!dbg::level(this->g.M, lo, hi, R)) return;
     if (!in_regs) fill();
     if (s & 1)
       tier<0>(a, ha, b, lo, hi, wall);
@@ -538,13 +544,19 @@ struct PDevCtx {
   __device__ __forceinline__ void sync() { __syncthreads(); }
   __device__ __forceinline__ T* row(int r, int c) { return sm + (r * Op::C + c) * g.M; }
   __device__ __forceinline__ void load_u(int r, int c, int j, int64_t x) {
-    row(r, c)[j] = __ldcg(u + c * g.N + wrap_n(x, g.N));
+    if (dbg::win(g.M, r, c, kC, j)) row(r, c)[j] = __ldcg(u + c * g.N + wrap_n(x, g.N));
   }
-  __device__ __forceinline__ void store_u(int r, int c, int j, int64_t x) { u[c * g.N + wrap_n(x, g.N)] = row(r, c)[j]; }
-  __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) { row(r, c)[j] = __ldcg(e_in + e); }
-  __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) { e_out[e] = row(r, c)[j]; }
+  __device__ __forceinline__ void store_u(int r, int c, int j, int64_t x) {
+    if (dbg::win(g.M, r, c, kC, j)) u[c * g.N + wrap_n(x, g.N)] = row(r, c)[j];
+  }
+  __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) {
+    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, g.nt * g.E, dbg::EDGE)) row(r, c)[j] = __ldcg(e_in + e);
+  }
+  __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) {
+    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, g.nt * g.E, dbg::EDGE)) e_out[e] = row(r, c)[j];
+  }
   __device__ __forceinline__ void level(int s, int, int lo, int hi, int64_t, int wall) {
-    LevelImpl<T, Op>::run(sm, g.M, stage_c<Op>(s), s & 1, lo, hi, wall, g.chunk, k);
+    if (dbg::level(g.M, lo, hi, kR)) LevelImpl<T, Op>::run(sm, g.M, stage_c<Op>(s), s & 1, lo, hi, wall, g.chunk, k);
     __syncthreads();
   }
 };
@@ -581,7 +593,8 @@ __global__ void __launch_bounds__(P > 0 ? 32 : 1024, P > 0 ? 16 : 1) k_swept_per
       int64_t dep_tile[3];
       int dep_need[3];
       const int ndep = persist_deps(g, n_sub, kp, b, dep_tile, dep_need);
-      for (int i = 0; ok && i < ndep; ++i) ok = persist_wait(ctl.done + dep_tile[i], dep_need[i], ctl);
+      for (int i = 0; ok && i < ndep; ++i)
+        ok = dbg::in_range(dep_tile[i], g.nt, dbg::COUNTER) && persist_wait(ctl.done + dep_tile[i], dep_need[i], ctl);
       if (!ok) atomicCAS(ctl.error, 0, 4);
       s_ok = ok;
       __threadfence();
@@ -641,19 +654,23 @@ struct ClusterCtx {
   __device__ __forceinline__ void sync() { __syncthreads(); }
   __device__ __forceinline__ T* row(int r, int c) { return sm + (r * Op::C + c) * g.M; }
   __device__ __forceinline__ void load_u(int r, int c, int j, int64_t x) {
-    row(r, c)[j] = __ldcg(u + c * g.N + wrap_n(x, g.N));
+    if (dbg::win(g.M, r, c, kC, j)) row(r, c)[j] = __ldcg(u + c * g.N + wrap_n(x, g.N));
   }
-  __device__ __forceinline__ void store_u(int r, int c, int j, int64_t x) { u[c * g.N + wrap_n(x, g.N)] = row(r, c)[j]; }
+  __device__ __forceinline__ void store_u(int r, int c, int j, int64_t x) {
+    if (dbg::win(g.M, r, c, kC, j)) u[c * g.N + wrap_n(x, g.N)] = row(r, c)[j];
+  }
   __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) {
+    if (!dbg::win(g.M, r, c, kC, j) || !dbg::in_range(e, g.nt * g.E, dbg::EDGE)) return;
     const unsigned tile = (unsigned)(e / g.E);
     const T* src = cooperative_groups::this_cluster().map_shared_rank(ex_in + (e - (int64_t)tile * g.E), tile);
     row(r, c)[j] = *src;
   }
   __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) {
-    ex_out[e - (int64_t)my_rank * g.E] = row(r, c)[j];
+    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e - (int64_t)my_rank * g.E, g.E, dbg::EDGE))
+      ex_out[e - (int64_t)my_rank * g.E] = row(r, c)[j];
   }
   __device__ __forceinline__ void level(int s, int, int lo, int hi, int64_t, int wall) {
-    LevelImpl<T, Op>::run(sm, g.M, stage_c<Op>(s), s & 1, lo, hi, wall, g.chunk, k);
+    if (dbg::level(g.M, lo, hi, kR)) LevelImpl<T, Op>::run(sm, g.M, stage_c<Op>(s), s & 1, lo, hi, wall, g.chunk, k);
     __syncthreads();
   }
 };
@@ -777,17 +794,22 @@ struct AdjCtx {
   __device__ __forceinline__ void sync() { __syncthreads(); }
   __device__ __forceinline__ T* row(int r, int c) { return sm + (r * AOp::C + c) * g.M; }
   __device__ __forceinline__ void load_u(int r, int c, int j, int64_t x) {
-    row(r, c)[j] = u_in[c * g.N + wrap_n(x, g.N)];
+    if (dbg::win(g.M, r, c, kC, j)) row(r, c)[j] = u_in[c * g.N + wrap_n(x, g.N)];
   }
   __device__ __forceinline__ void store_u(int r, int c, int j, int64_t x) {
-    u_out[c * g.N + wrap_n(x, g.N)] = row(r, c)[j];
+    if (dbg::win(g.M, r, c, kC, j)) u_out[c * g.N + wrap_n(x, g.N)] = row(r, c)[j];
   }
-  __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) { row(r, c)[j] = e_in[e]; }
-  __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) { e_out[e] = row(r, c)[j]; }
+  __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) {
+    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, g.nt * g.E, dbg::EDGE)) row(r, c)[j] = e_in[e];
+  }
+  __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) {
+    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, g.nt * g.E, dbg::EDGE)) e_out[e] = row(r, c)[j];
+  }
   __device__ __forceinline__ void level(int s, int b, int lo, int hi, int64_t origin, int wall) {
     const int64_t L = base + b + s;
-    adjoint_level<T, AOp>(sm, g.M, stage_c<AOp>(s), s & 1, lo, hi, wall, origin, g.N, tape + (top - L) * g.N, k,
-                          acc);
+    if (dbg::level(g.M, lo, hi, kR) && dbg::ok(top - L >= 0 && top - L <= top, dbg::TAPE, L))
+      adjoint_level<T, AOp>(sm, g.M, stage_c<AOp>(s), s & 1, lo, hi, wall, origin, g.N, tape + (top - L) * g.N, k,
+                            acc);
     __syncthreads();
   }
 };

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "debug_check.cuh"
 #include "ops.cuh"
 #include "swept2d.cuh"
 
@@ -14,6 +15,7 @@ namespace swept2d {
 using swept::add_rn;
 using swept::fma_rn;
 using swept::mul_rn;
+namespace dbg = swept::dbg;
 
 template <typename T>
 struct Heat2dK {
@@ -78,16 +80,32 @@ struct Dev2Ctx {
     else
       return *p;
   }
+  // debug build: window position and row, and a global coordinate within one
+  // period outside the grid (what wrap1 handles)
+  __device__ __forceinline__ bool win(int r, int lx, int ly) const {
+    return dbg::win(g.M, r, 0, 1, lx) && dbg::win(g.M, r, 0, 1, ly);
+  }
+  __device__ __forceinline__ bool coord(int64_t gx, int64_t gy) const {
+    return dbg::ok(gx >= -g.nx && gx < 2 * g.nx && gy >= -g.ny && gy < 2 * g.ny, dbg::STATE, gy * g.nx + gx);
+  }
   __device__ __forceinline__ void load_u(int r, int lx, int ly, int64_t gx, int64_t gy) {
-    at(r, lx, ly) = ld(u + gidx(gx, gy));
+    if (win(r, lx, ly) && coord(gx, gy)) at(r, lx, ly) = ld(u + gidx(gx, gy));
   }
   __device__ __forceinline__ void store_u(int r, int lx, int ly, int64_t gx, int64_t gy) {
-    u[gidx(gx, gy)] = at(r, lx, ly);
+    if (win(r, lx, ly) && coord(gx, gy)) u[gidx(gx, gy)] = at(r, lx, ly);
   }
-  __device__ __forceinline__ void load_strip(int r, int lx, int ly, int64_t e) { at(r, lx, ly) = ld(s_in + e); }
-  __device__ __forceinline__ void store_strip(int r, int lx, int ly, int64_t e) { s_out[e] = at(r, lx, ly); }
-  __device__ __forceinline__ void load_band(int r, int lx, int ly, int64_t e) { at(r, lx, ly) = ld(b_in + e); }
-  __device__ __forceinline__ void store_band(int r, int lx, int ly, int64_t e) { b_out[e] = at(r, lx, ly); }
+  __device__ __forceinline__ void load_strip(int r, int lx, int ly, int64_t e) {
+    if (win(r, lx, ly) && dbg::in_range(e, g.ntx * g.nty * g.Es, dbg::STRIP)) at(r, lx, ly) = ld(s_in + e);
+  }
+  __device__ __forceinline__ void store_strip(int r, int lx, int ly, int64_t e) {
+    if (win(r, lx, ly) && dbg::in_range(e, g.ntx * g.nty * g.Es, dbg::STRIP)) s_out[e] = at(r, lx, ly);
+  }
+  __device__ __forceinline__ void load_band(int r, int lx, int ly, int64_t e) {
+    if (win(r, lx, ly) && dbg::in_range(e, 2 * g.ntx * g.nty * g.Eb, dbg::BAND)) at(r, lx, ly) = ld(b_in + e);
+  }
+  __device__ __forceinline__ void store_band(int r, int lx, int ly, int64_t e) {
+    if (win(r, lx, ly) && dbg::in_range(e, 2 * g.ntx * g.nty * g.Eb, dbg::BAND)) b_out[e] = at(r, lx, ly);
+  }
   // level s on the local rectangle [x0, x1) x [y0, y1): row s & 1 from row
   // (s - 1) & 1.  The rectangle's points are spread flat over the block (point
   // i = y w + x to thread i mod blockDim), so narrow regions (bridges, small
@@ -99,8 +117,9 @@ struct Dev2Ctx {
     T* out = sm + (int64_t)(s & 1) * M * M;
     const int w = x1 - x0, n = w * (y1 - y0);
     const int t = (int)threadIdx.x, nt = (int)blockDim.x;
+    const bool in_window = dbg::level(M, x0, x1, kR) && dbg::level(M, y0, y1, kR);
     const int wx = axis_wall(g.bc, g.nx, ox, M), wy = axis_wall(g.bc, g.ny, oy, M);
-    if (t < n) {
+    if (in_window && t < n) {
       int y, x, dy, dx;
       const float rw = recip_small(w);
       divmod_small(t, w, rw, y, x);
@@ -213,7 +232,8 @@ __global__ void __launch_bounds__(1024) k_persist2d(Geom2 g, Heat2dK<T> k, T* u,
       int64_t index[4], need[4];
       const int nd = persist2d_deps(g, n, it, counter, index, need);
       for (int i = 0; ok && i < nd; ++i)
-        ok = persist2d_wait((counter[i] ? ctl.bridge_done : ctl.tile_done) + index[i], (int)need[i], ctl);
+        ok = dbg::in_range(index[i], (counter[i] ? 2 : 1) * g.ntx * g.nty, dbg::COUNTER) &&
+             persist2d_wait((counter[i] ? ctl.bridge_done : ctl.tile_done) + index[i], (int)need[i], ctl);
       if (!ok) atomicCAS(ctl.error, 0, 4);
       s_ok = ok;
       __threadfence();

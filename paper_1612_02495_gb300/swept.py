@@ -12,11 +12,13 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libswept.so")
+# SWEPT_DEBUG=1 selects the build with device-side index checks (include/swept.h, "Debug build")
+DEBUG_BUILD = os.environ.get("SWEPT_DEBUG", "0") == "1"
+LIB_PATH = os.path.join(HERE, "libswept_debug.so" if DEBUG_BUILD else "libswept.so")
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError("libswept.so is not built (run __graft_entry__.build() or "
-                      "python -m paper_1612_02495_gb300.build); the CUDA path has no fallback")
+    raise ImportError("%s is not built (run __graft_entry__.build() or python -m paper_1612_02495_gb300.build%s); "
+                      "the CUDA path has no fallback" % (os.path.basename(LIB_PATH), " --debug" if DEBUG_BUILD else ""))
 
 _lib = ctypes.CDLL(LIB_PATH)
 
@@ -424,6 +426,11 @@ classic2d_step_n = _sig("classic2d_step_n", [_H, _P, _I64, _P])
 swept2d_get_plan = _sig("swept2d_get_plan", [_H, ctypes.POINTER(swept2d_plan_info)])
 swept2d_check_schedule = _sig("swept2d_check_schedule", [_H, _I64, ctypes.POINTER(_I64)])
 swept2d_last_error = _sig("swept2d_last_error", [_H, ctypes.c_char_p, _SZ])
+swept_debug_status = _sig("swept_debug_status", [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                                  ctypes.POINTER(_I64)])
+swept_debug_probe = _sig("swept_debug_probe", [_P, _I64, _I64, _P])
+DEBUG_CHECK_NAMES = {1: "window", 2: "edge", 3: "level range", 4: "state coordinate", 5: "strip", 6: "band",
+                     7: "counter", 8: "tape slot", 9: "probe"}
 swept2d_set_option = _sig("swept2d_set_option", [_H, ctypes.c_int32, _I64])
 swept2d_sync_status = _sig("swept2d_sync_status", [_H, _P])
 SWEPT2D_OPT_CHECK_DROP_WAIT = 16
@@ -532,3 +539,16 @@ def check_schedule2d(dtype, nx, ny, tile_w, nsteps, threads=0, bc=BC_PERIODIC, p
         return n.value
     finally:
         swept2d_free(h.value)
+
+
+def debug_status():
+    """swept_debug_status: (enabled, None) when no check failed since the last
+    call, else (enabled, (check name, index)).  Raises SweptError(SWEPT_ECUDA)
+    if the device cannot be read."""
+    en, chk, idx = ctypes.c_int32(), ctypes.c_int32(), _I64()
+    st = swept_debug_status(ctypes.byref(en), ctypes.byref(chk), ctypes.byref(idx))
+    if st == SWEPT_OK:
+        return bool(en.value), None
+    if st == SWEPT_EDEVICE:
+        return bool(en.value), (DEBUG_CHECK_NAMES.get(chk.value, str(chk.value)), idx.value)
+    raise SweptError(st, "swept_debug_status")
