@@ -17,6 +17,7 @@ import argparse
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -92,7 +93,9 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index)
+        # raw samples: SWEPT_CLOCKS_DIR if set, else the system temporary folder
+        out_dir = os.environ.get("SWEPT_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, "swept_bench_clocks_rank%d.csv" % index)
 
     def start(self):
         try:
