@@ -1,5 +1,6 @@
 // C-ABI runtime of the 2D swept solver (include/swept2d.h): plan, workspace
-// layout, launch sequence of the swept and classic paths, CUDA-graph caching.
+// layout, launch sequence of the swept path (per pass, or the persistent queue
+// kernel) and of the classic path, CUDA-graph caching.
 #include <stdio.h>
 #include <string.h>
 
@@ -39,7 +40,7 @@ struct swept2d_handle {
 };
 
 namespace swept2d {
-// symbolic replay of the 2D launch sequence (check2d.cpp)
+// symbolic replay of the 2D launch sequence or persistent queue (check2d.cpp)
 bool check_schedule2d(const Geom2& g, int64_t nsteps, bool persistent, int64_t drop_wait, int64_t* computed,
                       std::string* err);
 }  // namespace swept2d

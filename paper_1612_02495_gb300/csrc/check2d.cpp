@@ -1,5 +1,5 @@
-// Host-side symbolic replay of the 2D swept launch sequence
-// (swept2d_check_schedule).
+// Host-side symbolic replay of the 2D swept launch sequence, or of the
+// persistent kernel's queue (swept2d_check_schedule).
 //
 // Runs the same phase code as the kernels (swept2d.cuh) over every block, with
 // buffers that hold (point, level) tags instead of values, and checks:
