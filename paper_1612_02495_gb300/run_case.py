@@ -2,6 +2,10 @@
 
   python -m paper_1612_02495_gb300.run_case --scheme ks|heat|euler|heat2d --dtype f64 --n 1048576 \\
       --nsteps 600 [--path swept|classic] [--tile 0] [--threads 0] [--chunk 0] [--persistent 0] [--cluster 0] [--warp-tiles 0] [--repeat 1]
+  python -m paper_1612_02495_gb300.run_case --scheme batch --dtype f32 --count 4096 [--tile 0] [--threads 0]
+      (the batched workload: count heat/KS problems, N = 2^U(10,18) rounded to 1024, 1,000-20,000 steps)
+  python -m paper_1612_02495_gb300.run_case --scheme ks --adjoint 1 --n 262144 --nsteps 5000
+      (FP64 heat / KS: the checkpointing forward solve, then the reverse sweep; times both)
 
 Used to profile a single kernel on a chosen size (e.g. under ncu).  One
 untimed warm-up solve precedes the timed repeats.
@@ -15,7 +19,7 @@ import numpy as np
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--scheme", default="ks", choices=["heat", "ks", "euler", "heat2d"])
+    ap.add_argument("--scheme", default="ks", choices=["heat", "ks", "euler", "heat2d", "batch"])
     ap.add_argument("--dtype", default="f64", choices=["f32", "f64"])
     ap.add_argument("--n", type=int, default=1 << 20)
     ap.add_argument("--nsteps", type=int, default=600)
@@ -27,6 +31,8 @@ def main(argv=None):
     ap.add_argument("--cluster", type=int, default=0)
     ap.add_argument("--warp-tiles", type=int, default=0)
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--count", type=int, default=4096, help="batch: number of problems")
+    ap.add_argument("--adjoint", type=int, default=0, help="heat / KS FP64: time the adjoint sweep")
     a = ap.parse_args(argv)
 
     import torch
@@ -38,6 +44,10 @@ def main(argv=None):
     dt_code = S.F64 if a.dtype == "f64" else S.F32
     if a.scheme == "heat2d":
         return run_heat2d(a, S, inputs, torch, npd, dt_code)
+    if a.scheme == "batch":
+        return run_batch(a, S, inputs, torch, npd, dt_code)
+    if a.adjoint:
+        return run_adjoint(a, S, inputs, torch)
     if a.scheme == "heat":
         p = inputs.heat_problem(n=a.n, dtype=npd)
         args = (S.HEAT, dt_code, a.n, p["dx"], p["dt"], p["alpha"], S.BC_PERIODIC)
@@ -98,6 +108,77 @@ def run_heat2d(a, S, inputs, torch, npd, dt_code):
     ms = float(np.median(times))
     print(json.dumps({"scheme": "heat2d", "dtype": a.dtype, "n": a.n, "nsteps": a.nsteps, "path": a.path,
                       "plan": sol.plan, "ms": ms, "cell_updates_per_s": a.n * a.n * a.nsteps / (ms * 1e-3)}))
+    sol.close()
+    return 0
+
+
+
+
+def _event_ms(torch, fn, repeat):
+    times = []
+    for _ in range(repeat):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return float(np.median(times))
+
+
+def run_batch(a, S, inputs, torch, npd, dt_code):
+    """The batched workload with a.count problems, one persistent launch per run."""
+    spec = inputs.batch_problems(count=a.count)
+    probs = inputs.batch_instances(spec, dtype=npd)
+    for q in probs:
+        q["tile_w"] = a.tile if a.tile and q["n"] % a.tile == 0 and q["n"] // a.tile >= 2 else 0
+    b = S.Batch(probs, dt_code, threads=a.threads)
+    u0 = b.pack([q["u0"] for q in probs])
+    u = u0.clone()
+    b.run(u)
+    torch.cuda.synchronize()
+
+    def once():
+        u.copy_(u0)
+        b.run(u)
+
+    ms = _event_ms(torch, once, a.repeat)
+    b.sync_status()
+    work = int((spec["n"] * spec["steps"]).sum())
+    print(json.dumps({"scheme": "batch", "dtype": a.dtype, "count": a.count, "items": b.items, "ms": ms,
+                      "cell_updates_per_s": work / (ms * 1e-3)}))
+    b.close()
+    return 0
+
+
+def run_adjoint(a, S, inputs, torch):
+    """FP64 heat or KS: the checkpointing forward solve and the reverse sweep."""
+    if a.scheme == "ks":
+        p = inputs.ks_problem(n=a.n)
+        sc, p0 = S.KS, p["nu"]
+    elif a.scheme == "heat":
+        p = inputs.heat_problem(n=a.n)
+        sc, p0 = S.HEAT, p["alpha"]
+    else:
+        raise SystemExit("the adjoint covers heat and KS")
+    sol = S.Solver(sc, S.F64, a.n, p["dx"], p["dt"], p0, tile_w=a.tile, threads=a.threads)
+    ckpt = torch.empty(sol.ckpt_size(a.nsteps), dtype=torch.uint8, device="cuda")
+    u0 = torch.from_numpy(p["u0"]).cuda()
+    gT = torch.from_numpy(inputs.rng(62).standard_normal(a.n)).cuda()
+    u = u0.clone()
+    sol.forward_ckpt(u, a.nsteps, ckpt)
+    sol.adjoint(gT, a.nsteps, ckpt)
+    torch.cuda.synchronize()
+
+    def fwd():
+        u.copy_(u0)
+        sol.forward_ckpt(u, a.nsteps, ckpt)
+
+    f_ms = _event_ms(torch, fwd, a.repeat)
+    b_ms = _event_ms(torch, lambda: sol.adjoint(gT, a.nsteps, ckpt), a.repeat)
+    sol.sync_status()
+    print(json.dumps({"scheme": a.scheme, "adjoint": 1, "n": a.n, "nsteps": a.nsteps, "plan": sol.plan,
+                      "forward_ckpt_ms": f_ms, "adjoint_ms": b_ms}))
     sol.close()
     return 0
 
