@@ -273,6 +273,39 @@ def test_persistent_mode_parity(S, scheme, dtype, n, W, threads, nsteps, bc):
     sol.close()
 
 
+def test_ks_full_size_in_the_bench_plan(S):
+    """KS N=2^20 FP64, 50,000 steps in the launch configuration bench.py times (the
+    autotuner's plan, from the same tune_single call): swept == classic bit for
+    bit, the mean is conserved, and sampled final points equal the oracle
+    advanced 100 steps from the GPU state at 49,900 steps on windows covering
+    their domain of dependence."""
+    import torch
+
+    from paper_1612_02495_gb300 import autotune
+
+    n, total, tail = 1 << 20, 50000, 100
+    plan = autotune.tune_single(S.KS, S.F64, n, probe_steps=4000)
+    p = inputs.ks_problem(n=n)
+    sol = autotune.solver_from_plan(S.KS, S.F64, n, p["dx"], p["dt"], p["nu"], plan)
+    u = torch.from_numpy(p["u0"]).cuda()
+    v, w = u.clone(), u.clone()
+    sol.step(u, total)
+    sol.classic(v, total)
+    sol.step(w, total - tail)
+    torch.cuda.synchronize()
+    sol.sync_status()
+    fin, mid = u.cpu().numpy(), w.cpu().numpy()
+    assert np.array_equal(fin, v.cpu().numpy()), plan
+    assert abs(fin.sum() - p["u0"].sum()) <= 1e-11 * np.abs(p["u0"]).sum()
+    reach = 2 * 2 * tail
+    rng = inputs.rng(98)
+    for c in rng.integers(0, n, size=8):
+        idx = (np.arange(c - reach - 8, c + reach + 9)) % n
+        loc = oracle.ks(mid[idx], p["dx"], p["dt"], p["nu"], tail)
+        assert loc[reach + 8] == fin[c], (plan, c, loc[reach + 8], fin[c])
+    sol.close()
+
+
 def test_persistent_full_size_ks(S):
     """KS N=2^20 FP64, 50,000 steps in the persistent kernel equals the per-pass path."""
     import torch
