@@ -148,7 +148,7 @@ def test_euler_parity(S, dtype, n, W, nsteps, bc):
 
 # --------------------------------------------------------------------------- full size, bench launch config
 def test_ks_full_size_sampled(S):
-    """KS N=2^20 FP64, 50,000 steps, default plan (the bench configuration):
+    """KS N=2^20 FP64, 50,000 steps, the library's default plan:
     swept == classic bit for bit; the mean is conserved; the whole field after
     the first 100 steps equals the oracle; and sampled points of the final
     state equal the oracle advanced 100 steps from the GPU state at 49,900
