@@ -45,7 +45,7 @@ def lib():
             getattr(L, "oracle_euler_run_" + sfx).argtypes = [_P, _I64, _D, _D, _D, _INT, _I64, _INT]
             getattr(L, "oracle_euler_stage_" + sfx).argtypes = [_P, _P, _I64, _D, _D, _D, _INT]
             getattr(L, "oracle_heat2d_run_" + sfx).argtypes = [_P, _I64, _I64, _D, _D, _D, _INT, _I64, _INT]
-        L.oracle_ks_adjoint_f64.argtypes = [_P, _I64, _D, _D, _D, _I64, _P, _P, _P, _I64, _P]
+        L.oracle_ks_adjoint_f64.argtypes = [_P, _I64, _D, _D, _D, _I64, _P, _P, _P, _I64, _P, _INT]
         L.oracle_heat_adjoint_f64.argtypes = [_P, _I64, _D, _D, _D, _INT, _I64, _P, _P, _P, _P]
         L.oracle_max_threads.restype = _INT
         _lib = L
@@ -121,15 +121,17 @@ def euler_stage(U0, dx, dt, gamma, bc=BC_MIRROR):
     return out
 
 
-def ks_adjoint(u0, dx, dt, nu, nsteps, gT, seg=0, with_condition=False):
+def ks_adjoint(u0, dx, dt, nu, nsteps, gT, seg=0, with_condition=False, threads=1):
     """Discrete adjoint of `ks` (FP64): returns (dL/du0, dL/dnu) for dL/du(T) = gT; with
-    with_condition, also the sum of the absolute values of dL/dnu's terms (its condition)."""
+    with_condition, also the sum of the absolute values of dL/dnu's terms (its condition).
+    seg = checkpoint segment length in steps (0: one segment); threads = OpenMP threads
+    (dL/du0 does not depend on it; dL/dnu only through its double-double rounding)."""
     u0 = np.ascontiguousarray(u0, dtype=np.float64)
     gT = np.ascontiguousarray(gT, dtype=np.float64)
     g = np.empty_like(u0)
     gnu = np.zeros(2)
     _check(lib().oracle_ks_adjoint_f64(_ptr(u0), u0.size, dx, dt, nu, nsteps, _ptr(gT), _ptr(g), _ptr(gnu[0:]), seg,
-                                       _ptr(gnu[1:])), "ks_adjoint")
+                                       _ptr(gnu[1:]), int(threads)), "ks_adjoint")
     return (g, float(gnu[0]), float(gnu[1])) if with_condition else (g, float(gnu[0]))
 
 

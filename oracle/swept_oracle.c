@@ -100,7 +100,13 @@ static inline int64_t nb_index(int64_t j, int64_t n, int bc, int* flip) {
  *   lam = fma(mdth, gT(mu; u), lam' + mu)         (mdth = -dt/2)
  * Parameter derivative (c_4 = nu k4, k4 = 1/dx^4, dg/dnu = k4 d4(w)):
  *   dL/dnu = sum_m sum_j [ -dt lam'_j k4 d4(P)_j - (dt/2) mu_j k4 d4(u^m)_j ]
- * accumulated in long double in the order m descending, j ascending.
+ * Each term is formed and added in double-double arithmetic (about 106
+ * significand bits: Knuth's TwoSum for sums, Dekker's exact product through
+ * fma), in the order m descending, j ascending, then rounded once to double.
+ * With threads > 1 each thread sums its own contiguous range of j over all m
+ * and the per-thread sums are added in thread order; the result then differs
+ * from the one-thread order only by the double-double rounding (~1e-32 of the
+ * condition below), far inside any tolerance built on that condition.
  * Also returned: the same sum with every factor replaced by its absolute
  * value and d4 by the absolute stencil |w_{j+2}| + 4|w_{j+1}| + 6|w_j| +
  * 4|w_{j-1}| + |w_{j-2}| -- the condition of the sum, which bounds the
@@ -122,11 +128,50 @@ static inline double ks_gT(const double* lam, const double* w, int64_t j, int64_
   return fma(c4, d4, fma(c2, d2, nl));
 }
 
-static inline long double ks_d4_abs(const double* w, int64_t j, int64_t n) {
-  return fabsl((long double)w[nb_index(j + 2, n, OR_BC_PERIODIC, NULL)]) +
-         4.0L * fabsl((long double)w[nb_index(j + 1, n, OR_BC_PERIODIC, NULL)]) + 6.0L * fabsl((long double)w[j]) +
-         4.0L * fabsl((long double)w[nb_index(j - 1, n, OR_BC_PERIODIC, NULL)]) +
-         fabsl((long double)w[nb_index(j - 2, n, OR_BC_PERIODIC, NULL)]);
+static inline double ks_d4_abs(const double* w, int64_t j, int64_t n) {
+  return fabs(w[nb_index(j + 2, n, OR_BC_PERIODIC, NULL)]) + 4.0 * fabs(w[nb_index(j + 1, n, OR_BC_PERIODIC, NULL)]) +
+         6.0 * fabs(w[j]) + 4.0 * fabs(w[nb_index(j - 1, n, OR_BC_PERIODIC, NULL)]) +
+         fabs(w[nb_index(j - 2, n, OR_BC_PERIODIC, NULL)]);
+}
+
+/* Double-double accumulation (value hi + lo, |lo| <= ulp(hi)/2). */
+typedef struct {
+  double hi, lo;
+} oracle_dd;
+
+/* Knuth's TwoSum: s + e == a + b exactly. */
+static inline oracle_dd dd_two_sum(double a, double b) {
+  const double s = a + b;
+  const double bp = s - a;
+  const double e = (a - (s - bp)) + (b - bp);
+  oracle_dd r = {s, e};
+  return r;
+}
+/* |a| >= |b| (or a == 0): s + e == a + b exactly. */
+static inline oracle_dd dd_fast_two_sum(double a, double b) {
+  const double s = a + b;
+  oracle_dd r = {s, b - (s - a)};
+  return r;
+}
+/* Dekker's exact product via fma: p + e == a * b exactly. */
+static inline oracle_dd dd_two_prod(double a, double b) {
+  const double p = a * b;
+  oracle_dd r = {p, fma(a, b, -p)};
+  return r;
+}
+static inline oracle_dd dd_mul_d(oracle_dd a, double b) {
+  oracle_dd p = dd_two_prod(a.hi, b);
+  return dd_fast_two_sum(p.hi, fma(a.lo, b, p.lo));
+}
+static inline oracle_dd dd_add(oracle_dd a, oracle_dd b) {
+  oracle_dd s = dd_two_sum(a.hi, b.hi);
+  const oracle_dd t = dd_two_sum(a.lo, b.lo);
+  s = dd_fast_two_sum(s.hi, s.lo + t.hi);
+  return dd_fast_two_sum(s.hi, s.lo + t.lo);
+}
+/* a * b * c * d as a double-double (relative error ~1e-32) */
+static inline oracle_dd dd_prod4(double a, double b, double c, double d) {
+  return dd_mul_d(dd_mul_d(dd_two_prod(a, b), c), d);
 }
 
 static inline double ks_d4(const double* w, int64_t j, int64_t n) {
@@ -138,16 +183,20 @@ static inline double ks_d4(const double* w, int64_t j, int64_t n) {
 /*
  * u0: initial state (n); gT: dL/du(T) (n).  Outputs g_u0 = dL/du0 (n) and
  * *g_nu = dL/dnu.  The forward states are recomputed from checkpoints taken
- * every `seg` steps (seg <= 0: one segment holding every state).
+ * every `seg` steps (seg <= 0: one segment holding every state).  The spatial
+ * loops use `threads` OpenMP threads; g_u0 does not depend on the thread
+ * count, *g_nu only through the double-double rounding (see above).
  */
 int oracle_ks_adjoint_f64(const double* u0, int64_t n, double dx, double dt, double nu, int64_t nsteps,
-                          const double* gT, double* g_u0, double* g_nu, int64_t seg, double* g_nu_abs) {
+                          const double* gT, double* g_u0, double* g_nu, int64_t seg, double* g_nu_abs, int threads) {
   if (!u0 || !gT || !g_u0 || !g_nu || n < 5 || nsteps < 0) return -1;
   if (seg <= 0 || seg > nsteps) seg = nsteps > 0 ? nsteps : 1;
+  if (threads < 1) threads = 1;
   const ks_consts_f64 k = ks_make_consts_f64(dx, dt, nu);
   const double idx2 = 1.0 / (dx * dx);
   const double k4 = idx2 * idx2;
   const double ca2 = 2.0 * k.ca;
+  const double mdt = -dt, mdth = -0.5 * dt;
   const int64_t nck = (nsteps + seg - 1) / seg + 1;
   double* ck = (double*)malloc((size_t)(nck * n) * sizeof(double));      /* checkpoints u^{c*seg} */
   double* tape_u = (double*)malloc((size_t)(seg * n) * sizeof(double));  /* u^m in a segment */
@@ -155,18 +204,19 @@ int oracle_ks_adjoint_f64(const double* u0, int64_t n, double dx, double dt, dou
   double* lam = (double*)malloc((size_t)n * sizeof(double));
   double* mu = (double*)malloc((size_t)n * sizeof(double));
   double* cur = (double*)malloc((size_t)n * sizeof(double));
-  if (!ck || !tape_u || !tape_p || !lam || !mu || !cur) {
-    free(ck); free(tape_u); free(tape_p); free(lam); free(mu); free(cur);
+  oracle_dd* part = (oracle_dd*)calloc((size_t)threads, sizeof(oracle_dd));   /* per-thread dL/dnu */
+  double* part_abs = (double*)calloc((size_t)threads, sizeof(double));         /* per-thread condition */
+  if (!ck || !tape_u || !tape_p || !lam || !mu || !cur || !part || !part_abs) {
+    free(ck); free(tape_u); free(tape_p); free(lam); free(mu); free(cur); free(part); free(part_abs);
     return -2;
   }
   /* forward sweep keeping checkpoints */
   memcpy(cur, u0, (size_t)n * sizeof(double));
   for (int64_t m = 0; m < nsteps; ++m) {
     if (m % seg == 0) memcpy(ck + (m / seg) * n, cur, (size_t)n * sizeof(double));
-    ks_step_f64(cur, mu, n, &k, 1);
+    ks_step_f64(cur, mu, n, &k, threads);
   }
   memcpy(lam, gT, (size_t)n * sizeof(double));
-  long double acc = 0.0L, acc_abs = 0.0L;
   const int64_t nseg = (nsteps + seg - 1) / seg;
   for (int64_t s = nseg - 1; s >= 0; --s) {
     const int64_t m0 = s * seg;
@@ -177,29 +227,54 @@ int oracle_ks_adjoint_f64(const double* u0, int64_t n, double dx, double dt, dou
       double* tu = tape_u + (m - m0) * n;
       double* tp = tape_p + (m - m0) * n;
       memcpy(tu, cur, (size_t)n * sizeof(double));
-      for (int64_t i = 0; i < n; ++i) tp[i] = fma(k.mdth, ks_g_f64(cur, i, n, k.ca, k.c2, k.c4), cur[i]);
-      for (int64_t i = 0; i < n; ++i) cur[i] = fma(k.mdt, ks_g_f64(tp, i, n, k.ca, k.c2, k.c4), cur[i]);
+      int64_t i;
+#pragma omp parallel for num_threads(threads) schedule(static) if (threads > 1)
+      for (i = 0; i < n; ++i) tp[i] = fma(k.mdth, ks_g_f64(cur, i, n, k.ca, k.c2, k.c4), cur[i]);
+#pragma omp parallel for num_threads(threads) schedule(static) if (threads > 1)
+      for (i = 0; i < n; ++i) cur[i] = fma(k.mdt, ks_g_f64(tp, i, n, k.ca, k.c2, k.c4), cur[i]);
     }
     /* reverse through the segment */
     for (int64_t m = m1 - 1; m >= m0; --m) {
       const double* tu = tape_u + (m - m0) * n;
       const double* tp = tape_p + (m - m0) * n;
-      for (int64_t j = 0; j < n; ++j) mu[j] = k.mdt * ks_gT(lam, tp, j, n, ca2, k.c2, k.c4);
-      for (int64_t j = 0; j < n; ++j) {
-        acc += (long double)(-dt) * (long double)lam[j] * (long double)k4 * (long double)ks_d4(tp, j, n);
-        acc += (long double)(-0.5 * dt) * (long double)mu[j] * (long double)k4 * (long double)ks_d4(tu, j, n);
-        acc_abs += (long double)dt * fabsl((long double)lam[j]) * (long double)k4 * ks_d4_abs(tp, j, n);
-        acc_abs += (long double)(0.5 * dt) * fabsl((long double)mu[j]) * (long double)k4 * ks_d4_abs(tu, j, n);
+#pragma omp parallel num_threads(threads) if (threads > 1)
+      {
+#ifdef _OPENMP
+        const int t = omp_get_thread_num();
+#else
+        const int t = 0;
+#endif
+        int64_t j;
+        oracle_dd acc_t = part[t];  /* thread-local copies: no false sharing in the loop */
+        double abs_t = part_abs[t];
+#pragma omp for schedule(static)
+        for (j = 0; j < n; ++j) mu[j] = k.mdt * ks_gT(lam, tp, j, n, ca2, k.c2, k.c4);
+        /* (implicit barrier: mu is complete before it is read by the stencil) */
+#pragma omp for schedule(static)
+        for (j = 0; j < n; ++j) {
+          acc_t = dd_add(acc_t, dd_prod4(mdt, lam[j], k4, ks_d4(tp, j, n)));
+          acc_t = dd_add(acc_t, dd_prod4(mdth, mu[j], k4, ks_d4(tu, j, n)));
+          abs_t += dt * fabs(lam[j]) * k4 * ks_d4_abs(tp, j, n);
+          abs_t += (0.5 * dt) * fabs(mu[j]) * k4 * ks_d4_abs(tu, j, n);
+          /* lam is read by the stencil, so compute into cur and copy back */
+          cur[j] = fma(k.mdth, ks_gT(mu, tu, j, n, ca2, k.c2, k.c4), lam[j] + mu[j]);
+        }
+        part[t] = acc_t;
+        part_abs[t] = abs_t;
       }
-      /* lam is read by the stencil, so compute into cur and copy back */
-      for (int64_t j = 0; j < n; ++j) cur[j] = fma(k.mdth, ks_gT(mu, tu, j, n, ca2, k.c2, k.c4), lam[j] + mu[j]);
       memcpy(lam, cur, (size_t)n * sizeof(double));
     }
   }
   memcpy(g_u0, lam, (size_t)n * sizeof(double));
-  *g_nu = (double)acc;
-  if (g_nu_abs) *g_nu_abs = (double)acc_abs;
-  free(ck); free(tape_u); free(tape_p); free(lam); free(mu); free(cur);
+  oracle_dd acc = {0.0, 0.0};
+  double acc_abs = 0.0;
+  for (int t = 0; t < threads; ++t) {
+    acc = dd_add(acc, part[t]);
+    acc_abs += part_abs[t];
+  }
+  *g_nu = acc.hi + acc.lo;
+  if (g_nu_abs) *g_nu_abs = acc_abs;
+  free(ck); free(tape_u); free(tape_p); free(lam); free(mu); free(cur); free(part); free(part_abs);
   return 0;
 }
 
