@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 
 N = 1 << 20
 NSTEPS = 50000
-METRIC = "cell-updates/s swept vs classic per-step GPU at 1 GB300"
+METRIC = "cell-updates/s swept vs classic per-step GPU at 1 GB300; adjoint/forward time"
 UNIT = "cell-updates/s"
 WORKLOAD = "Kuramoto-Sivashinsky N=2^20 FP64 periodic, 50,000 midpoint-RK2 steps (dt=0.005, dx=pi/4)"
 FP64_FLOPS_PER_SUBSTEP = 18  # 7 fma (2 flops) + 2 add + 2 mul per point per sub-timestep
@@ -43,11 +43,11 @@ FP64_INSTR_PEAK = 152 * 2 * 2.07e9
 # (python -m paper_1612_02495_gb300.peaks; the nominal rate needs constant-bank operands).
 FP64_KS_MIX_CEILING = 0.535e12
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_swept_diamond<double, KsOp> launch at
-# N = 2^20, tile 1024 (ncu, profiles/k_swept_diamond_ks_f64_n1048576.md); None once the kernel changes
+# N = 2^20, tile 1024, from an ncu capture; None: no capture of the current kernel
 DIAMOND_TRAFFIC_BYTES = None
-# same for one k_swept_persist<double, KsOp> launch of the bench's tuned plan (tile 1024, 512 threads,
-# a whole 50,000-step solve): 11.88 MB read + 36.98 MB written (ncu, one pass; the command is in
-# profiles/launches_bench_ks_f64_n1048576.md); None once the kernel or the plan changes
+# the same for one k_swept_persist<double, KsOp> launch (a whole 50,000-step solve) of the plan
+# (tile, threads) below: 11.88 MB read + 36.98 MB written in a one-pass ncu capture of just those
+# two counters; reported only when the tuned plan is that plan
 PERSIST_TRAFFIC_BYTES = 48860000
 PERSIST_TRAFFIC_PLAN = (1024, 512)  # (tile, threads) of that capture
 
@@ -135,8 +135,9 @@ class Clocks:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_rate(n, seconds, threads):
-    """Oracle cell-updates/s on a bounded window of the workload (grid N, few steps)."""
+def cpu_oracle_rate(n, seconds, threads, probe_only=False):
+    """Oracle cell-updates/s on a bounded window of the workload (grid N, few steps);
+    probe_only: return (None, steps, None) for the window a 2-step probe sizes to `seconds`."""
     import oracle
     from paper_1612_02495_gb300 import inputs
 
@@ -145,6 +146,8 @@ def cpu_oracle_rate(n, seconds, threads):
     oracle.ks(p["u0"], p["dx"], p["dt"], p["nu"], 2, threads=threads)
     per_step = max(time.perf_counter() - t0, 1e-6) / 2
     steps = int(max(2, min(100000, seconds / per_step)))
+    if probe_only:
+        return None, steps, None
     t0 = time.perf_counter()
     oracle.ks(p["u0"], p["dx"], p["dt"], p["nu"], steps, threads=threads)
     dt = time.perf_counter() - t0
@@ -369,23 +372,29 @@ def run_reference(args):
 
     threads = os.cpu_count() or 1
     oracle.build.build()
-    rates = []
-    steps_used = 0
+    import oracle as orc
+    from paper_1612_02495_gb300 import inputs
+
+    # one bench step = the oracle on the full N=2^20 grid for a fixed window of
+    # timesteps, sized once (from a 2-step probe) to about 8 s on these cores
+    _, window, _ = cpu_oracle_rate(N, 8.0, threads, probe_only=True)
+    p = inputs.ks_problem(n=N)
+    times = []
     for i in range(args.warmup + args.steps):
-        r, st, _ = cpu_oracle_rate(N, 8.0, threads)
+        t0 = time.perf_counter()
+        orc.ks(p["u0"], p["dx"], p["dt"], p["nu"], window, threads=threads)
+        dt = time.perf_counter() - t0
         if i >= args.warmup:
-            rates.append(r)
-            steps_used = st
-    v = float(np.mean(rates))
-    ms = N * NSTEPS / v * 1e3
+            times.append(dt)
+    ms = float(np.mean(times)) * 1e3
+    v = N * window / (ms * 1e-3)
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "n": N, "nsteps": NSTEPS, "oracle_window_steps": steps_used},
+           "config": {"workload": WORKLOAD, "n": N, "nsteps": NSTEPS, "oracle_window_steps": window},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                             "sample": "oracle (plain C, OpenMP over %d threads) on the full N=2^20 grid for a %d-step "
-                                      "window per bench step; ms_per_step extrapolates to 50,000 steps"
-                                      % (threads, steps_used)},
+                                      "window per bench step (ms_per_step is that window's time)" % (threads, window)},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
