@@ -68,13 +68,23 @@ typedef enum {
 
 /*
  * Problem and launch configuration.
- *   n        grid points (>= 2 * tile_w, and a multiple of tile_w)
+ *   n        grid points, any n >= 2r + 1 (r = 1 heat, 2 KS/Euler): the paper's
+ *            problem is a grid of n points, a stencil, a step count and a
+ *            boundary condition (Section "Test cases", Eq. HeatDisc, Eq. KSDisc).
+ *            The swept tiling takes floor(n / tile_w) >= 2 tiles; when tile_w
+ *            does not divide n, the last tile is wider by X = n mod tile_w
+ *            points (an up-trapezoid whose flat top of X points is handed from
+ *            pass to pass), so every diamond keeps height h.  A grid with no
+ *            legal tiling (n < 8r with tile_w = 0) still gets a handle, on which
+ *            classic_step_n runs and the swept calls return SWEPT_EUNSUPPORTED.
  *   dx, dt   grid spacing and timestep
  *   param[0] heat: alpha (diffusivity); KS: nu (factor on u_xxxx, 1 = the
  *            paper's equation); Euler: gamma
  *   tile_w   points per tile W (the paper's node size / threads per block);
- *            0 = chosen by the library.  Must be a multiple of 4*r (r = 1 heat,
- *            2 KS/Euler), so that the half-cycle h = W/(2r) is even.
+ *            0 = chosen by the library (a divisor of n when one gives enough
+ *            tiles).  Must be a multiple of 4*r (r = 1 heat, 2 KS/Euler), so
+ *            that the half-cycle h = W/(2r) is even, with n >= 2 W.  The cluster
+ *            and warp_tiles modes need W to divide n.
  *   threads  threads per block, 0 = chosen by the library (<= 1024, multiple of 32)
  *   chunk    heat and KS: 1 = one point per thread per trip through a tier
  *            (strided, the default); 2 = two strided points (j, j + threads)
@@ -133,6 +143,7 @@ typedef struct {
   int32_t persistent;      /* 1: persistent kernel */
   int32_t cluster;         /* 1: single-cluster kernel */
   int32_t warp_tiles;      /* 1: tier rows in registers, one warp per tile */
+  int32_t last_tile_extra; /* X = n - tiles * W: extra points of the last tile (0 when W divides n) */
 } swept_plan_info;
 
 typedef struct swept_handle swept_handle;
@@ -179,8 +190,10 @@ swept_status swept_run_host(swept_handle* h, const void* u_host_in, void* u_host
  * from checkpoints in ckpt_dev: u at the start of every segment of K steps,
  * plus one segment's tape of S*K + 1 tiers.  K is the largest whole number of
  * passes (h/S steps) whose layout fits ckpt_bytes; ckpt_bytes =
- * swept_adjoint_ckpt_size() gives K near sqrt(nsteps * h/S), and a buffer
- * large enough for K = nsteps stores the whole run and recomputes nothing.
+ * swept_adjoint_ckpt_size() is the smallest layout (K near sqrt(nsteps / S)
+ * rounded to whole passes: about 2 sqrt(S nsteps) + h copies of the state),
+ * and a buffer large enough for K = nsteps stores the whole run and
+ * recomputes nothing.  Any K recomputes each step at most once.
  * If u0_dev is NULL, the checkpoints and the last segment's tape written by the
  * most recent swept_forward_ckpt on this handle (same ckpt_dev, ckpt_bytes,
  * nsteps) are used, so only the earlier segments are recomputed; otherwise the
@@ -233,6 +246,14 @@ swept_status swept_batch_bind_workspace(swept_batch* b, void* ws_dev, size_t byt
 swept_status swept_batch_set_option(swept_batch* b, int32_t option, int64_t value);
 /* Advance every problem of the batch state u_dev by its nsteps, in place. */
 swept_status swept_batch_run(swept_batch* b, void* u_dev, void* stream);
+/* The same advance with the classic decomposition (Section "Classic scheme",
+ * Fig. ClassicCode), the baseline of swept_batch_run: launch k advances every
+ * problem that still has a sub-timestep k by one sub-timestep through global
+ * memory, one point per thread, with classic_step_n's per-point operation
+ * (results equal swept_batch_run bit for bit).  The launches are captured into
+ * CUDA graphs of 1024 launches, cached per u_dev.  It uses the tmp area of the
+ * bound workspace (one value per state value). */
+swept_status swept_batch_run_classic(swept_batch* b, void* u_dev, void* stream);
 /* Synchronize `stream`, then return SWEPT_ETIMEOUT if a bounded wait ran out. */
 swept_status swept_batch_sync_status(swept_batch* b, void* stream);
 swept_status swept_batch_last_error(const swept_batch* b, char* buf, size_t len);
@@ -247,24 +268,33 @@ void swept_batch_free(swept_batch* b);
 swept_status swept_profile_passes(swept_handle* h, void* u_dev, int64_t nsteps, void* stream, double* out_ms,
                                   int64_t* out_count);
 
+/* Size in bytes of the device array swept_step_n_static keeps its edge buffers in. */
+#define SWEPT_STATIC_SCRATCH_BYTES (8u << 20)
+
 /* Swept solve that allocates nothing, for callers that cannot call cudaMalloc
  * (their device memory belongs to an outside memory manager, or they run in a
  * loop where cudaMalloc/cudaFree would synchronise the device).  The paper has
  * no counterpart; it is swept_step_n with the edge buffers in one fixed 8 MiB
  * device array inside the library instead of a bound workspace, and without a
- * handle, graph or stream of its own.
+ * handle, graph or stream of its own.  The array is SWEPT_STATIC_SCRATCH_BYTES
+ * (8 MiB) long.
  *   cfg      as for swept_init, except that tile_w must be set (> 0); the
  *            launch options chunk, persistent, cluster and warp_tiles are
  *            ignored (one launch per pass, tiers in shared memory, one point
  *            per thread per trip), which changes no result
  *   u_dev    caller-owned state (layout above), advanced nsteps in place
- * The grid must fit the array: 4 * n * C * sizeof(value) <= 8 MiB (n <= 2^18 for
- * FP64 heat/KS, 2^19 for FP32); larger grids return SWEPT_ENOMEM_WORKSPACE and
- * launch nothing.  Results equal swept_step_n bit for bit.
+ * The grid must fit the array: 4 * n * C * sizeof(value) <= SWEPT_STATIC_SCRATCH_BYTES
+ * (n <= 2^18 for FP64 heat/KS, 2^19 for FP32); larger grids return
+ * SWEPT_ENOMEM_WORKSPACE and launch nothing.  Results equal swept_step_n bit
+ * for bit.  Tiles whose shared memory exceeds 48 KB raise the kernels' opt-in
+ * limit, never lower it, so handles with larger tiles keep working.
  * The first call on each device looks up the array's device address with that
- * device current; make that first call before any stream capture.  Every call
- * shares the one array (it keeps the last call's contents), so calls that
- * overlap on the GPU race; serialise them.
+ * device current and keeps it for the life of the process; make that first
+ * call before any stream capture.  cudaDeviceReset unloads the module, so the
+ * kept address is then stale: do not call this entry point again in a process
+ * that has reset a device it used.  Every call shares the one array (it keeps
+ * the last call's contents), so calls that overlap on the GPU race; serialise
+ * them.
  * Errors: SWEPT_EINVAL, SWEPT_ENOMEM_WORKSPACE, SWEPT_ECUDA. */
 swept_status swept_step_n_static(const swept_config* cfg, void* u_dev, int64_t nsteps, void* stream);
 

@@ -29,13 +29,16 @@ def _radius(scheme):
 
 
 def tile_candidates(scheme, n, max_w=1024, min_w=None):
-    """Legal tile widths: multiples of 4r that divide n with at least 2 tiles
-    (powers of two, or n's other divisors when n is not a power of two);
-    widths below min_w (default: 32, or 64 from 2^16 points on) are skipped."""
+    """Legal tile widths: multiples of 4r with at least 2 tiles.  Widths that
+    divide n come first (powers of two, or n's other divisors when n is not a
+    power of two); when no multiple of 4r divides n, the powers of two among
+    the legal widths (the last tile then carries the n mod W extra points).
+    Widths below min_w (default: 32, or 64 from 2^16 points on) are skipped."""
     q = 4 * _radius(scheme)
     if min_w is None:
         min_w = 64 if n >= (1 << 16) else 32
-    out = [w for w in range(q, max_w + 1, q) if n % w == 0 and n // w >= 2 and w >= min(min_w, n // 2)]
+    legal = [w for w in range(q, max_w + 1, q) if n // w >= 2 and w >= min(min_w, max(q, n // 2))]
+    out = [w for w in legal if n % w == 0] or legal
     pw = [w for w in out if w & (w - 1) == 0]
     return pw if pw else out
 
@@ -97,11 +100,12 @@ def _time(fn, reps):
     return best
 
 
-def warp_tile_ok(scheme, W):
+def warp_tile_ok(scheme, W, n=None):
     """Tile widths the register (warp-tile) mapping supports: W = 32 P with
-    P in {1, 2, 4, 8} and at least r points per lane; heat and KS only."""
+    P in {1, 2, 4, 8} and at least r points per lane, dividing n; heat and KS only."""
     P = W // 32
-    return scheme != S.EULER and W % 32 == 0 and P in (1, 2, 4, 8) and P >= _radius(scheme)
+    return (scheme != S.EULER and W % 32 == 0 and P in (1, 2, 4, 8) and P >= _radius(scheme)
+            and (n is None or n % W == 0))
 
 
 def tune_single(scheme, dtype, n, probe_steps=None, cache=DEFAULT_CACHE, refresh=False, reps=2, threads=THREADS,
@@ -125,11 +129,11 @@ def tune_single(scheme, dtype, n, probe_steps=None, cache=DEFAULT_CACHE, refresh
     d0 = torch.from_numpy(np.ascontiguousarray(u0)).cuda()
     for W in tile_candidates(scheme, n):
         mappings = [(t, 0) for t in threads if t <= max(32, 2 * W)]
-        if warp_tiles and warp_tile_ok(scheme, W):
+        if warp_tiles and warp_tile_ok(scheme, W, n):
             mappings.append((32, 1))
         for t, wt in mappings:
             for mode in modes:
-                if mode == 2 and n // W > MAX_CLUSTER_TILES:
+                if mode == 2 and (n // W > MAX_CLUSTER_TILES or n % W):
                     continue
                 try:
                     sol = S.Solver(scheme, dtype, n, *args, bc=bc, tile_w=W, threads=t, persistent=int(mode == 1),

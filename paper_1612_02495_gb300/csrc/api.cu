@@ -9,6 +9,7 @@
 #include <vector>
 
 #include <algorithm>
+#include <mutex>
 
 #include "graph_cache.h"
 #include "kernels.cuh"
@@ -44,22 +45,35 @@ const SchemeImpl* pick_impl(int scheme, int dtype) {
   }
 }
 
-bool tile_ok(int64_t n, int W, int R) { return W >= 4 * R && W % (4 * R) == 0 && n % W == 0 && n / W >= 2; }
+// A tile width is legal when it is a multiple of 4R (so the half cycle h =
+// W/(2R) is even and the tips meet at whole points) and the grid holds at
+// least two tiles; a grid that is not a multiple of W gets a wider last tile.
+bool tile_ok(int64_t n, int W, int R) { return W >= 4 * R && W % (4 * R) == 0 && n / W >= 2; }
+bool tile_divides(int64_t n, int W, int R) { return tile_ok(n, W, R) && n % W == 0; }
 
 // Default tile width: the largest W <= 1024 (multiple of 4R, dividing n) that
 // still gives at least two blocks per SM; else at least one per SM; else the
-// smallest legal W.
+// smallest such W.  When no multiple of 4R divides n, the same rules choose
+// among all legal widths (the last tile then carries the n mod W extra points).
 int choose_tile(int64_t n, int R, int sms) {
-  int best = 0;
-  for (int W = 4 * R; W <= 1024; W += 4 * R)
-    if (tile_ok(n, W, R) && n / W >= 2 * sms) best = W;
-  if (best) return best;
-  for (int W = 4 * R; W <= 1024; W += 4 * R)
-    if (tile_ok(n, W, R) && n / W >= sms) best = W;
-  if (best) return best;
-  for (int W = 4 * R; W <= 4096; W += 4 * R)
-    if (tile_ok(n, W, R)) return W;
+  for (int pass = 0; pass < 2; ++pass) {
+    auto ok = [&](int W) { return pass == 0 ? tile_divides(n, W, R) : tile_ok(n, W, R); };
+    int best = 0;
+    for (int W = 4 * R; W <= 1024; W += 4 * R)
+      if (ok(W) && n / W >= 2 * sms) best = W;
+    if (best) return best;
+    for (int W = 4 * R; W <= 1024; W += 4 * R)
+      if (ok(W) && n / W >= sms) best = W;
+    if (best) return best;
+    for (int W = 4 * R; W <= 4096; W += 4 * R)
+      if (ok(W)) return W;
+  }
   return 0;
+}
+
+swept_status no_tiling(swept_handle* h) {
+  return fail(h, SWEPT_EUNSUPPORTED, "grid too small for a swept tiling (fewer than two tiles of 4r points): "
+                                     "only classic_step_n runs on this handle");
 }
 
 
@@ -168,15 +182,22 @@ AdjPlan adj_layout(const swept_handle* h, int64_t nsteps, int64_t K) {
   return a;
 }
 
-// steps per segment: whole passes (h/S steps) or the whole run; for a size
-// query (bytes == 0) about sqrt(nsteps * h/S), else the largest that fits
+// steps per segment: whole passes (h/S steps) or the whole run.  For a size
+// query (bytes == 0) the segment that needs the least memory: the buffer holds
+// ceil(nsteps / K) checkpoints plus a tape of S K + 1 tiers, smallest near
+// K = sqrt(nsteps / S), and every choice recomputes each step once.  Otherwise
+// the largest segment that fits `bytes`.
 int64_t adj_segment(const swept_handle* h, int64_t nsteps, size_t bytes) {
   const int64_t K0 = h->g.h / h->g.S;
   if (nsteps <= K0) return nsteps;
   if (bytes == 0) {
-    int64_t m = 1;
-    while ((m + 1) * (m + 1) * K0 <= nsteps) ++m;
-    return std::min<int64_t>(nsteps, m * K0);
+    int64_t best = nsteps;
+    size_t best_bytes = adj_layout(h, nsteps, nsteps).bytes;
+    for (int64_t K = K0; K < nsteps; K += K0) {
+      const size_t b = adj_layout(h, nsteps, K).bytes;
+      if (b < best_bytes) best = K, best_bytes = b;
+    }
+    return best;
   }
   if (adj_layout(h, nsteps, nsteps).bytes <= bytes) return nsteps;
   for (int64_t K = (nsteps / K0) * K0; K >= K0; K -= K0)
@@ -242,6 +263,7 @@ cudaError_t issue_adjoint(swept_handle* h, const void* ka, void* lam, int64_t n_
 swept_status adj_check(swept_handle* h, int64_t nsteps, void* ckpt, size_t bytes, AdjPlan* plan) {
   if (!h->impl->adj_up || h->cfg.dtype != SWEPT_F64)
     return fail(h, SWEPT_EUNSUPPORTED, "the adjoint exists for heat and KS in FP64 only");
+  if (!h->tiled) return no_tiling(h);
   if (!ckpt || nsteps < 0 || ((uintptr_t)ckpt % kAlign) != 0)
     return fail(h, SWEPT_EINVAL, "ckpt_dev NULL or not 256-byte aligned, or nsteps < 0");
   const int64_t K = adj_segment(h, nsteps, bytes);
@@ -286,7 +308,7 @@ swept_status swept_init(const swept_config* cfg, swept_handle** out) {
   if (!im) return SWEPT_EINVAL;
   if (cfg->bc != SWEPT_BC_PERIODIC && cfg->bc != SWEPT_BC_REFLECTIVE) return SWEPT_EINVAL;
   if (cfg->scheme == SWEPT_KS && cfg->bc != SWEPT_BC_PERIODIC) return SWEPT_EINVAL;
-  if (!(cfg->dx > 0) || !(cfg->dt > 0) || cfg->n < 8) return SWEPT_EINVAL;
+  if (!(cfg->dx > 0) || !(cfg->dt > 0) || cfg->n < 2 * im->R + 1) return SWEPT_EINVAL;
   if (cfg->scheme == SWEPT_EULER && !(cfg->param[0] > 1.0)) return SWEPT_EINVAL;
   swept_handle* h = new (std::nothrow) swept_handle();
   if (!h) return SWEPT_EINVAL;
@@ -311,22 +333,28 @@ swept_status swept_init(const swept_config* cfg, swept_handle** out) {
   cudaGetLastError();  // clear a no-device error
   cudaError_t e = cudaSuccess;
   const int R = im->R;
-  int W = cfg->tile_w > 0 ? cfg->tile_w : choose_tile(cfg->n, R, h->sm_count);
-  if (W <= 0 || !tile_ok(cfg->n, W, R)) {
+  const int W = cfg->tile_w > 0 ? cfg->tile_w : choose_tile(cfg->n, R, h->sm_count);
+  // an explicit tile must be legal; with the library's choice, a grid too
+  // small for two tiles of 4R points still gets a handle for classic_step_n
+  if (cfg->tile_w != 0 && (cfg->tile_w < 0 || !tile_ok(cfg->n, W, R))) {
     delete h;
     return SWEPT_EINVAL;
   }
+  h->tiled = W > 0;
   Geom& g = h->g;
   g.N = cfg->n;
-  g.W = W;
   g.R = R;
   g.S = im->S;
   g.C = im->C;
-  g.h = W / (2 * R);
-  g.M = W + 2 * R;
-  g.nt = cfg->n / W;
-  g.E = 2 * g.h * g.C * 2 * R;
   g.bc = cfg->bc;
+  if (h->tiled) {
+    g.W = W;
+    g.h = W / (2 * R);
+    g.nt = cfg->n / W;
+    g.X = (int)(cfg->n - g.nt * W);
+    g.M = W + g.X + 2 * R;
+    g.E = 2 * g.h * g.C * 2 * R;
+  }
   // one point per thread per tier unless asked: on GB300 the register-window
   // mapping measured slower at every size (the tiers are latency-bound, and
   // spreading a tier over more warps beats fewer shared-memory reads)
@@ -336,7 +364,7 @@ swept_status swept_init(const swept_config* cfg, swept_handle** out) {
     delete h;
     return SWEPT_EINVAL;
   }
-  int th = cfg->threads > 0 ? cfg->threads : (W >= 256 ? 256 : ((W + 31) / 32) * 32);
+  int th = cfg->threads > 0 ? cfg->threads : (W >= 256 ? 256 : std::max(32, ((W + 31) / 32) * 32));
   if (th < 32 || th > 1024 || th % 32 != 0) {
     delete h;
     return SWEPT_EINVAL;
@@ -348,8 +376,8 @@ swept_status swept_init(const swept_config* cfg, swept_handle** out) {
   }
   if (cfg->warp_tiles == 1) {
     const int P = W / 32;
-    if (im->C != 1 || W % 32 != 0 || (P != 1 && P != 2 && P != 4 && P != 8) || P < R || g.chunk != 1 ||
-        (cfg->threads != 0 && cfg->threads != 32)) {
+    if (!h->tiled || g.X != 0 || im->C != 1 || W % 32 != 0 || (P != 1 && P != 2 && P != 4 && P != 8) || P < R ||
+        g.chunk != 1 || (cfg->threads != 0 && cfg->threads != 32)) {
       delete h;
       return SWEPT_EINVAL;
     }
@@ -357,14 +385,14 @@ swept_status swept_init(const swept_config* cfg, swept_handle** out) {
     th = 32;
   }
   h->threads = th;
-  h->smem = (size_t)im->smem_values(g.M) * im->value_bytes;
+  h->smem = h->tiled ? (size_t)im->smem_values(g.M) * im->value_bytes : 0;
   if (h->smem > (size_t)max_smem) {
     delete h;
     return SWEPT_EINVAL;
   }
   im->make_consts(cfg->param, cfg->dx, cfg->dt, h->k);
   const size_t vb = (size_t)im->value_bytes;
-  const size_t ebytes = align_up((size_t)g.nt * g.E * vb);
+  const size_t ebytes = align_up((size_t)swept::edge_slots(g) * g.E * vb);
   h->off_e0 = 0;
   h->off_e1 = ebytes;
   h->off_tmp = 2 * ebytes;
@@ -381,7 +409,11 @@ swept_status swept_init(const swept_config* cfg, swept_handle** out) {
     return SWEPT_EINVAL;
   }
   h->cluster = cfg->cluster == 1;
-  if (h->cluster && (g.nt > 16 || h->persistent ||
+  if ((h->persistent || h->cluster) && !h->tiled) {
+    delete h;
+    return SWEPT_EINVAL;
+  }
+  if (h->cluster && (g.nt > 16 || g.X != 0 || h->persistent ||
                      h->smem + 2 * (size_t)g.E * im->value_bytes > (size_t)max_smem)) {
     delete h;
     return SWEPT_EINVAL;
@@ -414,7 +446,9 @@ swept_status swept_bind_workspace(swept_handle* h, void* ws_dev, size_t bytes) {
 swept_status swept_step_n(swept_handle* h, void* u_dev, int64_t nsteps, void* stream) {
   const swept_trace::Range trace_range("swept_step_n");
   swept_status st = check_ready(h, u_dev, nsteps);
-  if (st != SWEPT_OK || nsteps == 0) return st;
+  if (st != SWEPT_OK) return st;
+  if (!h->tiled) return no_tiling(h);
+  if (nsteps == 0) return st;
   const cudaStream_t s = (cudaStream_t)stream;
   const int64_t n_sub = nsteps * h->g.S;
   if (h->cluster) {
@@ -502,6 +536,7 @@ swept_status swept_run_host(swept_handle* h, const void* u_host_in, void* u_host
   const swept_trace::Range trace_range("swept_run_host");
   if (!h) return SWEPT_EINVAL;
   if (!u_host_in || !u_host_out) return fail(h, SWEPT_EINVAL, "host buffer is NULL");
+  if (use_swept && !h->tiled) return no_tiling(h);
   swept_status st = check_ready(h, u_dev, nsteps);
   if (st != SWEPT_OK) return st;
   const cudaStream_t s = (cudaStream_t)stream;
@@ -518,7 +553,7 @@ swept_status swept_run_host(swept_handle* h, const void* u_host_in, void* u_host
 
 swept_status swept_adjoint_ckpt_size(const swept_handle* h, int64_t nsteps, size_t* bytes) {
   if (!h || !bytes || nsteps < 0) return SWEPT_EINVAL;
-  if (!h->impl->adj_up || h->cfg.dtype != SWEPT_F64) return SWEPT_EUNSUPPORTED;
+  if (!h->impl->adj_up || h->cfg.dtype != SWEPT_F64 || !h->tiled) return SWEPT_EUNSUPPORTED;
   *bytes = adj_layout(h, nsteps, std::max<int64_t>(1, adj_segment(h, nsteps, 0))).bytes;
   return SWEPT_OK;
 }
@@ -592,6 +627,7 @@ swept_status swept_profile_passes(swept_handle* h, void* u_dev, int64_t nsteps, 
                                   int64_t* out_count) {
   swept_status st = check_ready(h, u_dev, nsteps);
   if (st != SWEPT_OK) return st;
+  if (!h->tiled) return no_tiling(h);
   if (!out_ms || !out_count) return fail(h, SWEPT_EINVAL, "NULL output arrays");
   for (int i = 0; i < 4; ++i) {
     out_ms[i] = 0.0;
@@ -643,6 +679,7 @@ swept_status swept_get_plan(const swept_handle* h, swept_plan_info* out) {
   out->persistent = h->persistent ? 1 : 0;
   out->cluster = h->cluster ? 1 : 0;
   out->warp_tiles = h->g.P > 0 ? 1 : 0;
+  out->last_tile_extra = h->g.X;
   return SWEPT_OK;
 }
 
@@ -662,6 +699,18 @@ swept_status swept_sync_status(swept_handle* h, void* stream) {
 }  // extern "C"
 
 namespace swept {
+
+cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, fn);
+  if (e != cudaSuccess) return e;
+  if ((size_t)a.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 namespace dbg {
 namespace {
 std::vector<FetchFn>& fetchers() {
@@ -726,6 +775,7 @@ swept_status swept_set_option(swept_handle* h, int32_t option, int64_t value) {
 
 swept_status swept_check_schedule(swept_handle* h, int64_t nsteps, int64_t* computed_out) {
   if (!h || nsteps < 0) return SWEPT_EINVAL;
+  if (!h->tiled) return no_tiling(h);
   return swept::check_schedule(h, nsteps, computed_out);
 }
 

@@ -11,6 +11,7 @@
 #include <string>
 
 #include "graph_cache.h"
+#include "impl.h"
 #include "kernels2d.cuh"
 #include "swept2d.h"
 #include "trace.h"
@@ -81,13 +82,10 @@ using swept_graphs::key_of;
 
 template <typename T>
 cudaError_t prepare_t(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(swept2d::k_pyr2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(swept2d::k_bridge2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(swept2d::k_octa2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(swept2d::k_persist2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = swept::raise_smem_limit((const void*)swept2d::k_pyr2d<T>, smem);
+  if (e == cudaSuccess) e = swept::raise_smem_limit((const void*)swept2d::k_bridge2d<T>, smem);
+  if (e == cudaSuccess) e = swept::raise_smem_limit((const void*)swept2d::k_octa2d<T>, smem);
+  if (e == cudaSuccess) e = swept::raise_smem_limit((const void*)swept2d::k_persist2d<T>, smem);
   return e;
 }
 

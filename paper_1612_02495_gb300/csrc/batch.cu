@@ -43,6 +43,8 @@ struct BatchProb {
   int64_t u_off;   // first value of this problem in the state array
   int64_t e_off;   // first value of this problem's two edge buffers
   int64_t t0;      // first tile counter of this problem
+  int64_t cblk0;   // first block of this problem in the classic launches
+  int64_t n_sub;   // sub-timesteps (nsteps * S)
   int32_t kind;    // SWEPT_HEAT / SWEPT_KS
   int32_t W, h, R, S;
   int32_t q, rem, npass;
@@ -90,10 +92,10 @@ struct BatchCtx {
     if (dbg::win(g.M, r, c, kC, j)) u[c * g.N + wrap_n(x, g.N)] = row(r, c)[j];
   }
   __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) {
-    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, g.nt * g.E, dbg::EDGE)) row(r, c)[j] = __ldcg(e_in + e);
+    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, edge_slots(g) * g.E, dbg::EDGE)) row(r, c)[j] = __ldcg(e_in + e);
   }
   __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) {
-    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, g.nt * g.E, dbg::EDGE)) e_out[e] = row(r, c)[j];
+    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, edge_slots(g) * g.E, dbg::EDGE)) e_out[e] = row(r, c)[j];
   }
   __device__ __forceinline__ void level(int s, int, int lo, int hi, int64_t, int wall) {
     if (!dbg::level(g.M, lo, hi, kR))
@@ -228,6 +230,68 @@ __global__ void __launch_bounds__(1024) k_batch(BatchDev d, T* u_all, T* e_all) 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Classic decomposition of a batch (the baseline of the batched swept solver):
+// launch k advances every problem that still has a sub-timestep k, one point
+// per thread, through global memory (Section "Classic scheme"), with the same
+// per-point operation as classic_step_n.  Problems are ordered by sub-timestep
+// count, longest first, so the active problems of launch k are a prefix and
+// the launch covers the blocks [0, cblk(k)).  kBatchClassicBlock points per
+// block, each block inside one problem (blk_prob).  A heat problem alternates
+// u -> tmp (even k) and tmp -> u (odd k); a KS problem runs stage k mod 2:
+// u -> tmp (predictor), then tmp, u -> u.
+// ---------------------------------------------------------------------------
+constexpr int kBatchClassicBlock = 256;
+
+template <typename T, class Op, int STAGE>
+__device__ __forceinline__ void classic_point(const BatchProb& p, int64_t i, const T* in, T* out) {
+  constexpr int R = Op::R;
+  typename Op::K k;
+  memcpy(&k, p.k, sizeof(k));
+  T v[2 * R + 1];
+  if (i >= R && i < p.n - R) {
+#pragma unroll
+    for (int d = 0; d <= 2 * R; ++d) v[d] = in[i + d - R];
+  } else {
+#pragma unroll
+    for (int d = 0; d <= 2 * R; ++d) v[d] = in[wrap_n(i + d - R, p.n)];
+  }
+  const T p2 = STAGE == 1 ? out[i] : T(0);
+  out[i] = Op::template point<STAGE>(v, p2, k);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBatchClassicBlock) k_classic_batch(const BatchProb* probs, const int32_t* blk_prob,
+                                                                      int64_t k, T* u_all, T* t_all) {
+  const BatchProb& p = probs[blk_prob[blockIdx.x]];
+  const int64_t i = ((int64_t)blockIdx.x - p.cblk0) * kBatchClassicBlock + threadIdx.x;
+  if (i >= p.n) return;
+  T* u = u_all + p.u_off;
+  T* t = t_all + p.u_off;
+  if (p.kind == SWEPT_HEAT) {
+    if ((k & 1) == 0)
+      classic_point<T, HeatOp<T>, 0>(p, i, u, t);
+    else
+      classic_point<T, HeatOp<T>, 0>(p, i, t, u);
+  } else {
+    if ((k & 1) == 0)
+      classic_point<T, KsOp<T>, 0>(p, i, u, t);
+    else
+      classic_point<T, KsOp<T>, 1>(p, i, t, u);
+  }
+}
+
+// a heat problem with an odd sub-timestep count ends in tmp: copy it back
+template <typename T>
+__global__ void __launch_bounds__(kBatchClassicBlock) k_classic_batch_finish(const BatchProb* probs,
+                                                                             const int32_t* blk_prob, T* u_all,
+                                                                             const T* t_all) {
+  const BatchProb& p = probs[blk_prob[blockIdx.x]];
+  if (p.kind != SWEPT_HEAT || (p.n_sub & 1) == 0) return;
+  const int64_t i = ((int64_t)blockIdx.x - p.cblk0) * kBatchClassicBlock + threadIdx.x;
+  if (i < p.n) u_all[p.u_off + i] = t_all[p.u_off + i];
+}
+
 }  // namespace
 }  // namespace swept
 
@@ -254,6 +318,14 @@ struct swept_batch {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
   const void* exec_u = nullptr;
+  // classic baseline: blocks of launch k are [0, cblk_end[k]) (problems sorted
+  // by sub-timestep count, longest first); graphs of kClassicChunk launches
+  std::vector<int32_t> blk_prob;
+  std::vector<int64_t> cblk_end;
+  int64_t max_sub = 0;
+  size_t off_blk = 0, off_tmp = 0;
+  std::vector<cudaGraphExec_t> cexec;
+  const void* cexec_u = nullptr;
   std::string err;
 };
 
@@ -271,6 +343,39 @@ void drop_graph(swept_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   b->exec = nullptr;
   b->exec_u = nullptr;
+  for (cudaGraphExec_t x : b->cexec) cudaGraphExecDestroy(x);
+  b->cexec.clear();
+  b->cexec_u = nullptr;
+}
+
+constexpr int64_t kClassicChunk = 1024;  // classic launches per captured graph
+
+// classic launches [k0, k1) of the batch (and the final copy when k1 is the end)
+cudaError_t launch_classic(swept_batch* b, void* u, int64_t k0, int64_t k1, cudaStream_t s) {
+  const BatchProb* probs = (const BatchProb*)(b->ws + b->off_probs);
+  const int32_t* bp = (const int32_t*)(b->ws + b->off_blk);
+  for (int64_t k = k0; k < k1; ++k) {
+    const unsigned grid = (unsigned)b->cblk_end[(size_t)k];
+    if (b->dtype == SWEPT_F64)
+      swept::k_classic_batch<double><<<grid, swept::kBatchClassicBlock, 0, s>>>(probs, bp, k, (double*)u,
+                                                                                (double*)(b->ws + b->off_tmp));
+    else
+      swept::k_classic_batch<float><<<grid, swept::kBatchClassicBlock, 0, s>>>(probs, bp, k, (float*)u,
+                                                                               (float*)(b->ws + b->off_tmp));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (k1 == b->max_sub && !b->blk_prob.empty()) {
+    const unsigned grid = (unsigned)b->blk_prob.size();
+    if (b->dtype == SWEPT_F64)
+      swept::k_classic_batch_finish<double><<<grid, swept::kBatchClassicBlock, 0, s>>>(
+          probs, bp, (double*)u, (const double*)(b->ws + b->off_tmp));
+    else
+      swept::k_classic_batch_finish<float><<<grid, swept::kBatchClassicBlock, 0, s>>>(
+          probs, bp, (float*)u, (const float*)(b->ws + b->off_tmp));
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
 }
 
 int default_batch_tile(int64_t n, int R) {
@@ -352,6 +457,7 @@ swept_status swept_batch_plan(const swept_batch_problem* problems, int64_t count
     p.u_off = u_off;
     b->offsets[(size_t)i] = u_off;
     u_off += (q.n + 63) / 64 * 64;  // 256-byte aligned starts in FP32 and FP64
+    p.n_sub = n_sub;
     p.e_off = e_off;
     e_off += 2 * p.nt * (int64_t)(2 * p.h * 2 * R);
     p.t0 = t0;
@@ -362,6 +468,27 @@ swept_status swept_batch_plan(const swept_batch_problem* problems, int64_t count
   b->state_values = u_off;
   b->edge_values = e_off;
   b->total_tiles = t0;
+  // classic baseline: problems by sub-timestep count, longest first; each
+  // problem's points in whole blocks of kBatchClassicBlock
+  {
+    std::vector<int64_t> order((size_t)count);
+    for (int64_t i = 0; i < count; ++i) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t c) {
+      return b->probs[(size_t)a].n_sub > b->probs[(size_t)c].n_sub;
+    });
+    b->max_sub = b->probs[(size_t)order[0]].n_sub;
+    b->cblk_end.assign((size_t)b->max_sub, 0);
+    int64_t blk = 0;
+    for (int64_t j = 0; j < count; ++j) {
+      BatchProb& p = b->probs[(size_t)order[(size_t)j]];
+      p.cblk0 = blk;
+      const int64_t nb = (p.n + swept::kBatchClassicBlock - 1) / swept::kBatchClassicBlock;
+      for (int64_t x = 0; x < nb; ++x) b->blk_prob.push_back((int32_t)order[(size_t)j]);
+      blk += nb;
+      // launches k < n_sub of this problem cover its blocks (the prefix grows)
+      for (int64_t k = 0; k < p.n_sub; ++k) b->cblk_end[(size_t)k] = blk;
+    }
+  }
   // groups: layer k, problem p, with nt_p items each
   int maxpass = 0;
   for (auto& p : b->probs) maxpass = std::max(maxpass, (int)p.npass);
@@ -399,6 +526,10 @@ swept_status swept_batch_plan(const swept_batch_problem* problems, int64_t count
   off += kAlign;
   b->off_edges = off;
   off = align_up(off + (size_t)b->edge_values * vb);
+  b->off_blk = off;
+  off = align_up(off + b->blk_prob.size() * sizeof(int32_t));
+  b->off_tmp = off;
+  off = align_up(off + (size_t)b->state_values * vb);
   b->ws_bytes = off;
   int dev = -1;
   if (cudaGetDevice(&dev) == cudaSuccess) {
@@ -440,13 +571,14 @@ swept_status swept_batch_bind_workspace(swept_batch* b, void* ws_dev, size_t byt
     e = cudaMemcpy(b->ws + b->off_gprob, b->gprob.data(), b->gprob.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(b->ws + b->off_gpass, b->gpass.data(), b->gpass.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !b->blk_prob.empty())
+    e = cudaMemcpy(b->ws + b->off_blk, b->blk_prob.data(), b->blk_prob.size() * sizeof(int32_t),
+                   cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return bfail(b, SWEPT_ECUDA, std::string("upload: ") + cudaGetErrorString(e));
   // persistent grid: at most the co-resident blocks
   const void* fn = b->dtype == SWEPT_F64 ? (const void*)swept::k_batch<double> : (const void*)swept::k_batch<float>;
-  if (b->smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
-    if (e != cudaSuccess) return bfail(b, SWEPT_ECUDA, "shared-memory limit");
-  }
+  e = swept::raise_smem_limit(fn, b->smem);
+  if (e != cudaSuccess) return bfail(b, SWEPT_ECUDA, "shared-memory limit");
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, b->threads, b->smem);
   if (e != cudaSuccess || per_sm < 1) return bfail(b, SWEPT_EINVAL, "batch kernel does not fit on an SM");
@@ -487,7 +619,9 @@ swept_status swept_batch_run(swept_batch* b, void* u_dev, void* stream) {
     return e == cudaSuccess ? SWEPT_OK : bfail(b, SWEPT_ECUDA, cudaGetErrorString(e));
   }
   if (!b->exec || b->exec_u != u_dev) {
-    drop_graph(b);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    b->exec_u = nullptr;
     e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return bfail(b, SWEPT_ECUDA, "begin capture");
     cudaError_t le = launch_batch(b, u_dev, b->cap);
@@ -504,6 +638,48 @@ swept_status swept_batch_run(swept_batch* b, void* u_dev, void* stream) {
   }
   e = cudaGraphLaunch(b->exec, s);
   return e == cudaSuccess ? SWEPT_OK : bfail(b, SWEPT_ECUDA, cudaGetErrorString(e));
+}
+
+swept_status swept_batch_run_classic(swept_batch* b, void* u_dev, void* stream) {
+  const swept_trace::Range trace_range("swept_batch_run_classic");
+  if (!b || !u_dev) return SWEPT_EINVAL;
+  if (!b->ws) return bfail(b, SWEPT_ENOWORKSPACE, "no workspace bound");
+  if (b->max_sub == 0) return SWEPT_OK;
+  const cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cs);
+  if (e != cudaSuccess) return bfail(b, SWEPT_ECUDA, "cudaStreamIsCapturing");
+  if (cs != cudaStreamCaptureStatusNone) {
+    e = launch_classic(b, u_dev, 0, b->max_sub, s);
+    return e == cudaSuccess ? SWEPT_OK : bfail(b, SWEPT_ECUDA, cudaGetErrorString(e));
+  }
+  if (b->cexec.empty() || b->cexec_u != u_dev) {
+    for (cudaGraphExec_t x : b->cexec) cudaGraphExecDestroy(x);
+    b->cexec.clear();
+    for (int64_t k0 = 0; k0 < b->max_sub; k0 += kClassicChunk) {
+      const int64_t k1 = std::min(b->max_sub, k0 + kClassicChunk);
+      e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return bfail(b, SWEPT_ECUDA, "begin capture");
+      const cudaError_t le = launch_classic(b, u_dev, k0, k1, b->cap);
+      cudaGraph_t g = nullptr;
+      e = cudaStreamEndCapture(b->cap, &g);
+      if (le != cudaSuccess || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bfail(b, SWEPT_ECUDA, cudaGetErrorString(le != cudaSuccess ? le : e));
+      }
+      cudaGraphExec_t x = nullptr;
+      e = cudaGraphInstantiate(&x, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return bfail(b, SWEPT_ECUDA, "graph instantiate");
+      b->cexec.push_back(x);
+    }
+    b->cexec_u = u_dev;
+  }
+  for (cudaGraphExec_t x : b->cexec) {
+    e = cudaGraphLaunch(x, s);
+    if (e != cudaSuccess) return bfail(b, SWEPT_ECUDA, cudaGetErrorString(e));
+  }
+  return SWEPT_OK;
 }
 
 swept_status swept_batch_sync_status(swept_batch* b, void* stream) {

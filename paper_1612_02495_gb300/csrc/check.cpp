@@ -249,8 +249,8 @@ void init_sim(Sim& sim, const Geom& g, int64_t n_sub) {
   for (int c = 0; c < g.C; ++c)
     for (int64_t x = 0; x < g.N; ++x) sim.u[(size_t)(c * g.N + x)] = Tag{x, 0};
   for (int b = 0; b < 2; ++b) {
-    sim.e[b].assign((size_t)g.nt * g.E, Tag{});
-    sim.ae[b].assign((size_t)g.nt * g.E, Access{});
+    sim.e[b].assign((size_t)edge_slots(g) * g.E, Tag{});
+    sim.ae[b].assign((size_t)edge_slots(g) * g.E, Access{});
   }
   sim.au.assign((size_t)g.C * g.N, Access{});
   sim.count.assign((size_t)(n_sub + 1) * g.N, 0);
@@ -276,8 +276,8 @@ swept_status check_persistent(swept_handle* h, int64_t nsteps, int64_t* computed
   const size_t words = (size_t)((items + 63) / 64);
   sim.anc.assign((size_t)items, std::vector<uint64_t>(words, 0));
   sim.hb[BUF_U].assign((size_t)g.C * g.N, HbLoc{});
-  sim.hb[BUF_E0].assign((size_t)g.nt * g.E, HbLoc{});
-  sim.hb[BUF_E1].assign((size_t)g.nt * g.E, HbLoc{});
+  sim.hb[BUF_E0].assign((size_t)edge_slots(g) * g.E, HbLoc{});
+  sim.hb[BUF_E1].assign((size_t)edge_slots(g) * g.E, HbLoc{});
   for (int64_t it = 0; it < items && sim.err.empty(); ++it) {
     const int kp = (int)(it / g.nt);
     const int64_t b = it - (int64_t)kp * g.nt;

@@ -55,6 +55,13 @@ struct SchemeImpl {
                              double* slots, cudaStream_t s);
 };
 
+// Raise kernel `fn`'s dynamic shared-memory limit on the current device to at
+// least `bytes` (when bytes > 48 KB).  It never lowers the limit: every handle
+// and every static call shares the kernel instantiations, so a smaller tile
+// must not take away the opt-in a larger tile's handle set up earlier.  The
+// read-check-set runs under one process-wide lock.
+cudaError_t raise_smem_limit(const void* fn, size_t bytes);
+
 const SchemeImpl* heat_impl(int dtype);
 const SchemeImpl* ks_impl(int dtype);
 const SchemeImpl* euler_impl(int dtype);

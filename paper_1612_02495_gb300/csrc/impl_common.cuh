@@ -33,9 +33,9 @@ struct Launch {
     return cudaErrorInvalidValue;
   }
   static cudaError_t prepare(size_t bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_swept_up<T, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = raise_smem_limit((const void*)k_swept_up<T, Op>, bytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_swept_diamond<T, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return raise_smem_limit((const void*)k_swept_diamond<T, Op>, bytes);
   }
   static cudaError_t up(const Geom& g, const void* k, const void* u_in, void* u_out, void* e_out, int hh,
                         int write_top, int threads, size_t smem, cudaStream_t s) {
@@ -73,11 +73,8 @@ struct Launch {
                              int blocks, int threads, size_t smem, cudaStream_t s) {
     return with_p(g.P, [&](auto pc) {
       constexpr int P = decltype(pc)::value;
-      if (smem > 48 * 1024) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_swept_persist<T, Op, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-      }
+      cudaError_t e = raise_smem_limit((const void*)k_swept_persist<T, Op, P>, smem);
+      if (e != cudaSuccess) return e;
       PersistCtl c{done, queue, error, spin_limit, start_item};
       k_swept_persist<T, Op, P><<<blocks, threads, smem, s>>>(g, kc(k), (T*)u, (T*)e0, (T*)e1, n_sub, c);
       return cudaGetLastError();
@@ -87,11 +84,8 @@ struct Launch {
     int n = 0;
     const cudaError_t e = with_p(P_, [&](auto pc) {
       constexpr int P = decltype(pc)::value;
-      if (smem > 48 * 1024) {
-        cudaError_t e2 =
-            cudaFuncSetAttribute(k_swept_persist<T, Op, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e2 != cudaSuccess) return e2;
-      }
+      cudaError_t e2 = raise_smem_limit((const void*)k_swept_persist<T, Op, P>, smem);
+      if (e2 != cudaSuccess) return e2;
       return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_swept_persist<T, Op, P>, threads, smem);
     });
     return e == cudaSuccess ? n : 0;
@@ -108,8 +102,7 @@ struct Launch {
     const size_t bytes = smem + 2 * (size_t)g.E * sizeof(T);
     auto fn = k_swept_cluster<T, Op, P>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e == cudaSuccess && bytes > 48 * 1024)
-      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) e = raise_smem_limit((const void*)fn, bytes);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)g.nt, 1, 1);
@@ -134,11 +127,9 @@ struct Launch {
     return t;
   }
   static cudaError_t prepare_tape(size_t bytes) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_swept_up_tape<T, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = raise_smem_limit((const void*)k_swept_up_tape<T, Op>, bytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_swept_diamond_tape<T, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)bytes);
+    return raise_smem_limit((const void*)k_swept_diamond_tape<T, Op>, bytes);
   }
   static cudaError_t up_tape(const Geom& g, const void* k, const void* u_in, void* u_out, void* e_out, int hh,
                              int write_top, int threads, size_t smem, void* tape, int64_t tier0, int64_t ntiers,
@@ -173,9 +164,9 @@ struct AdjLaunch {
     return kk;
   }
   static cudaError_t prepare(size_t bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_adj_up<T, AOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = raise_smem_limit((const void*)k_adj_up<T, AOp>, bytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_adj_diamond<T, AOp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return raise_smem_limit((const void*)k_adj_diamond<T, AOp>, bytes);
   }
   static cudaError_t up(const Geom& g, const void* ka, const void* lam_in, void* lam_out, void* e_out, int hh,
                         int write_top, int threads, size_t smem, const void* tape, int64_t top, int64_t base,

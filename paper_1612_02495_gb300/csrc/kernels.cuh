@@ -354,10 +354,10 @@ struct DevCtx {
     if (dbg::win(g.M, r, c, kC, j)) u_out[c * g.N + wrap_n(x, g.N)] = row(r, c)[j];
   }
   __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) {
-    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, g.nt * g.E, dbg::EDGE)) row(r, c)[j] = e_in[e];
+    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, edge_slots(g) * g.E, dbg::EDGE)) row(r, c)[j] = e_in[e];
   }
   __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) {
-    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, g.nt * g.E, dbg::EDGE)) e_out[e] = row(r, c)[j];
+    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, edge_slots(g) * g.E, dbg::EDGE)) e_out[e] = row(r, c)[j];
   }
   __device__ __forceinline__ void level(int s, int base, int lo, int hi, int64_t origin, int wall) {
     if (dbg::level(g.M, lo, hi, kR)) LevelImpl<T, Op>::run(sm, g.M, stage_c<Op>(s), s & 1, lo, hi, wall, g.chunk, k);
@@ -550,10 +550,10 @@ struct PDevCtx {
     if (dbg::win(g.M, r, c, kC, j)) u[c * g.N + wrap_n(x, g.N)] = row(r, c)[j];
   }
   __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) {
-    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, g.nt * g.E, dbg::EDGE)) row(r, c)[j] = __ldcg(e_in + e);
+    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, edge_slots(g) * g.E, dbg::EDGE)) row(r, c)[j] = __ldcg(e_in + e);
   }
   __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) {
-    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, g.nt * g.E, dbg::EDGE)) e_out[e] = row(r, c)[j];
+    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, edge_slots(g) * g.E, dbg::EDGE)) e_out[e] = row(r, c)[j];
   }
   __device__ __forceinline__ void level(int s, int, int lo, int hi, int64_t, int wall) {
     if (dbg::level(g.M, lo, hi, kR)) LevelImpl<T, Op>::run(sm, g.M, stage_c<Op>(s), s & 1, lo, hi, wall, g.chunk, k);
@@ -660,7 +660,7 @@ struct ClusterCtx {
     if (dbg::win(g.M, r, c, kC, j)) u[c * g.N + wrap_n(x, g.N)] = row(r, c)[j];
   }
   __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) {
-    if (!dbg::win(g.M, r, c, kC, j) || !dbg::in_range(e, g.nt * g.E, dbg::EDGE)) return;
+    if (!dbg::win(g.M, r, c, kC, j) || !dbg::in_range(e, edge_slots(g) * g.E, dbg::EDGE)) return;
     const unsigned tile = (unsigned)(e / g.E);
     const T* src = cooperative_groups::this_cluster().map_shared_rank(ex_in + (e - (int64_t)tile * g.E), tile);
     row(r, c)[j] = *src;
@@ -800,10 +800,10 @@ struct AdjCtx {
     if (dbg::win(g.M, r, c, kC, j)) u_out[c * g.N + wrap_n(x, g.N)] = row(r, c)[j];
   }
   __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) {
-    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, g.nt * g.E, dbg::EDGE)) row(r, c)[j] = e_in[e];
+    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, edge_slots(g) * g.E, dbg::EDGE)) row(r, c)[j] = e_in[e];
   }
   __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) {
-    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, g.nt * g.E, dbg::EDGE)) e_out[e] = row(r, c)[j];
+    if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, edge_slots(g) * g.E, dbg::EDGE)) e_out[e] = row(r, c)[j];
   }
   __device__ __forceinline__ void level(int s, int b, int lo, int hi, int64_t origin, int wall) {
     const int64_t L = base + b + s;

@@ -25,7 +25,7 @@
 
 namespace {
 
-constexpr size_t kStaticScratchBytes = size_t(8) << 20;  // 8 MiB
+constexpr size_t kStaticScratchBytes = SWEPT_STATIC_SCRATCH_BYTES;  // 8 MiB (include/swept.h)
 constexpr size_t kAlign = 256;
 constexpr int kMaxDevices = 64;
 
@@ -98,7 +98,7 @@ extern "C" swept_status swept_step_n_static(const swept_config* cfg, void* u_dev
     return SWEPT_ECUDA;
   const size_t smem = (size_t)im->smem_values(g.M) * im->value_bytes;
   if (smem > (size_t)max_smem) return SWEPT_EINVAL;
-  if (smem > 48 * 1024 && im->prepare(smem) != cudaSuccess) return SWEPT_ECUDA;
+  if (smem > 48 * 1024 && im->prepare(smem) != cudaSuccess) return SWEPT_ECUDA;  // raises only
   void* scratch = nullptr;
   if (scratch_on(dev, &scratch) != cudaSuccess) return SWEPT_ECUDA;
   void* eb[2] = {scratch, (char*)scratch + ebytes};

@@ -25,6 +25,7 @@ struct swept_handle {
   size_t ws_bound = 0;   // bound size
   size_t off_e0 = 0, off_e1 = 0, off_tmp = 0, off_status = 0;
   size_t off_persist = 0;  // nt tile counters, then queue counter and error word
+  bool tiled = true;  // false: the grid is too small for a swept tiling (classic only)
   bool persistent = false;
   bool cluster = false;
   int persist_blocks = 0;  // co-resident blocks of the persistent kernel (0 = not yet queried)

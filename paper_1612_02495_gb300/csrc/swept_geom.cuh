@@ -16,9 +16,22 @@
 //     it spans a whole tile shifted by W/2, and then shrinks that tile again;
 //   - passes alternate between boundaries at (b+1) W (odd pass: tiles move
 //     right by W/2) and b W + W/2 (even pass: tiles move back), the zig-zag.
-// Local coordinates: a block's window is M = W + 2R points; a tile sits at
+// Local coordinates: a block's window is W + 2R points; a tile sits at
 // local [R, W + R); a diamond window centred on c sits at global
 // [c - W/2 - R, c + W/2 + R).
+//
+// Grids that are not a multiple of W (the problem statement fixes only a grid
+// of n points): the last tile, nt - 1, is wider by X = n - nt W points
+// (0 < X < W).  Its triangle cannot close, so it is a trapezoid whose top
+// (X points at tier h, the "flat top") is complete at the end of the pass.
+// Every pass hands that flat top to block nt - 1 of the next pass (one more
+// slot, index nt, in the edge buffers), whose tile is then the W-wide diamond
+// plus the flat top: on the left of the diamond in odd passes (the tiling
+// shifted right by W/2), on its right in even passes.  The shrink of a wide
+// tile stops at tier h with a new flat top in the middle of the tile.  All
+// diamonds keep height h, so the zig-zag is unchanged; only block nt - 1 of
+// every up, diamond and down pass does the extra X points per tier.  The
+// remainder's gap passes are plain W windows around the tile boundaries.
 #pragma once
 #include <stdint.h>
 
@@ -42,12 +55,22 @@ struct Geom {
   int S;       // sub-timesteps (stages) per timestep
   int C;       // values per point
   int h;       // W / (2R): sub-timesteps per pass
-  int M;       // W + 2R: window width
+  int M;       // W + X + 2R: window width (the row stride; W + 2R when X = 0)
   int E;       // values per tile in an edge buffer: 2 sides * h * C * 2R
   int bc;      // 0 periodic, 1 mirror walls at -1/2 and N-1/2
   int chunk;   // consecutive points one thread advances per tier (1 = strided mapping)
   int P = 0;   // tiers in registers: points per lane of the one warp that owns a tile (0 = in shared memory)
+  int X = 0;   // extra width of the last tile (N - nt W, 0 <= X < W)
 };
+
+// edge-buffer slots per buffer: one per tile, plus the flat-top slot when X > 0
+SW_HD int64_t edge_slots(const Geom& g) { return g.nt + (g.X > 0 ? 1 : 0); }
+// first point of tile b of the unshifted tiling (b = nt gives N)
+SW_HD int64_t tile_start(const Geom& g, int64_t b) { return b < g.nt ? b * (int64_t)g.W : g.N; }
+// width of tile b (the same for the tile of block b in the shifted tiling)
+SW_HD int tile_width(const Geom& g, int64_t b) { return g.W + (b == g.nt - 1 ? g.X : 0); }
+// offset of flat-top value k (0..X-1) of component c in an edge buffer
+SW_HD int64_t top_index(const Geom& g, int c, int k) { return g.nt * (int64_t)g.E + (int64_t)c * g.X + k; }
 
 SW_HD int64_t floor_div(int64_t a, int64_t b) {
   int64_t q = a / b;
@@ -87,10 +110,11 @@ SW_HD int up_hi(const Geom& g, int s) { return g.W + g.R - g.R * s; }
 SW_HD int grow_lo(const Geom& g, int s) { return g.W / 2 + g.R - g.R * s; }
 SW_HD int grow_hi(const Geom& g, int s) { return g.W / 2 + g.R + g.R * s; }
 
-// edge k (0..2R-1) of level s of a tile, side 0 = left end, 1 = right end
-SW_HD int edge_pos(const Geom& g, int side, int s, int k) {
-  return side == 0 ? g.R + g.R * s + k : g.W - g.R - g.R * s + k;
+// edge k (0..2R-1) of level s of a tile of width w, side 0 = left end, 1 = right end
+SW_HD int edge_pos(const Geom& g, int side, int s, int k, int w) {
+  return side == 0 ? g.R + g.R * s + k : w - g.R - g.R * s + k;
 }
+SW_HD int edge_pos(const Geom& g, int side, int s, int k) { return edge_pos(g, side, s, k, g.W); }
 // where an edge lands in the diamond window: the right edges (side 1) of the
 // tile left of c, and the left edges (side 0) of the tile right of c
 SW_HD int insert_pos(const Geom& g, int side, int s, int k) {
@@ -109,11 +133,11 @@ SW_HD int64_t left_tile(const Geom& g, int odd, int64_t b) { return odd ? b : (b
 SW_HD int64_t right_tile(const Geom& g, int odd, int64_t b) { return odd ? (b + 1) % g.nt : b; }
 
 // Local index of the first point after a mirror wall (x = k N) inside the
-// window [origin, origin + M), or NO_WALL (periodic, or no wall inside).
-SW_HD int window_wall(const Geom& g, int64_t origin) {
+// window [origin, origin + m), or NO_WALL (periodic, or no wall inside).
+SW_HD int window_wall(const Geom& g, int64_t origin, int m) {
   if (g.bc == 0) return NO_WALL;
   const int64_t xw = (floor_div(origin, g.N) + 1) * g.N;
-  return (xw < origin + g.M) ? (int)(xw - origin) : NO_WALL;
+  return (xw < origin + m) ? (int)(xw - origin) : NO_WALL;
 }
 // position read for neighbour offset d of point j: across a wall, the mirror
 // image (the boundary rule applied at the split node, Section "First-order")

@@ -23,18 +23,21 @@ namespace swept {
 // Up-triangle (pass 0, Fig. SweptPseudo) or, with hh < h, the trapezoid that
 // starts the remainder: load tile b from u, compute tiers 1..hh, export the
 // 2R edge values of tiers 0..hh-1 on both sides; with write_top, also write
-// tier hh (the trapezoid's top, non-empty when hh < h) back to u.
+// tier hh (the trapezoid's top, non-empty when hh < h) back to u.  The wide
+// last tile (X > 0) is a trapezoid even at hh = h; without write_top it
+// exports its flat top (tier h) to the flat-top slot of edges_out.
 template <class Cx>
 SW_HD void run_up(Cx& cx, const Geom& g_in, int64_t b, int hh, bool write_top) {
   const Geom g = fixed_geom<Cx>(g_in);
+  const int w = tile_width(g, b);
   const int64_t x0 = b * (int64_t)g.W;
   const int64_t origin = x0 - g.R;
-  cx.for_range(0, g.W * g.C, [&](int i) {
-    const int c = g.C == 1 ? 0 : i / g.W, k = i - c * g.W;
+  cx.for_range(0, w * g.C, [&](int i) {
+    const int c = g.C == 1 ? 0 : i / w, k = i - c * w;
     cx.load_u(0, c, g.R + k, x0 + k);
   });
   cx.sync();
-  for (int s = 1; s <= hh; ++s) cx.level(s, 0, up_lo(g, s), up_hi(g, s), origin, NO_WALL);
+  for (int s = 1; s <= hh; ++s) cx.level(s, 0, g.R + g.R * s, g.R + w - g.R * s, origin, NO_WALL);
   const int per_level = g.C * 2 * g.R;
   const int per_side = hh * per_level;
   cx.for_range(0, 2 * per_side, [&](int i) {
@@ -43,15 +46,21 @@ SW_HD void run_up(Cx& cx, const Geom& g_in, int64_t b, int hh, bool write_top) {
     const int s = rem / per_level;
     const int c = (rem - s * per_level) / (2 * g.R);
     const int k = rem % (2 * g.R);
-    cx.store_edge(s & 1, c, edge_pos(g, side, s, k), edge_index(g, b, side, s, c, k));
+    cx.store_edge(s & 1, c, edge_pos(g, side, s, k, w), edge_index(g, b, side, s, c, k));
   });
   if (write_top) {
-    const int lo = up_lo(g, hh), w = up_hi(g, hh) - lo;
-    if (w > 0)
-      cx.for_range(0, w * g.C, [&](int i) {
-        const int c = g.C == 1 ? 0 : i / w, k = i - c * w;
+    const int lo = g.R + g.R * hh, tw = w - 2 * g.R * hh;
+    if (tw > 0)
+      cx.for_range(0, tw * g.C, [&](int i) {
+        const int c = g.C == 1 ? 0 : i / tw, k = i - c * tw;
         cx.store_u(hh & 1, c, lo + k, origin + lo + k);
       });
+  } else if (w > g.W && hh == g.h) {
+    const int lo = g.R + g.W / 2;
+    cx.for_range(0, g.X * g.C, [&](int i) {
+      const int c = g.C == 1 ? 0 : i / g.X, k = i - c * g.X;
+      cx.store_edge(g.h & 1, c, lo + k, top_index(g, c, k));
+    });
   }
 }
 
@@ -63,11 +72,20 @@ SW_HD void run_up(Cx& cx, const Geom& g_in, int64_t b, int hh, bool write_top) {
 //                 point where a full tier exists, Section "First-order");
 //   MODE_GAP:     hh < h, write the grown gap [c - R hh, c + R hh) of tier hh
 //                 (completes the remainder trapezoids).
+// Block nt - 1 of a diamond or down pass on a grid with X > 0 owns the wide
+// tile: it also inserts the previous pass's flat top (tier h) beside its
+// diamond, and in MODE_DIAMOND shrinks through tier h and exports the new
+// flat top.
 template <class Cx>
 SW_HD void run_diamond(Cx& cx, const Geom& g_in, int64_t b, int odd, int mode, int hh) {
   const Geom g = fixed_geom<Cx>(g_in);
-  const int64_t c = pass_center(g, odd, b);
-  const int64_t origin = c - g.W / 2 - g.R;
+  const bool wide = g.X > 0 && b == g.nt - 1 && mode != MODE_GAP;
+  const int w = wide ? g.W + g.X : g.W;  // width of this block's tile
+  const int dofs = wide && odd ? g.X : 0;  // the diamond's offset inside the tile (flat top on its left)
+  // first point of the block's tile: odd passes shift the tiling right by W/2;
+  // a gap window is the plain window around boundary (b + 1) W (N for b = nt - 1)
+  const int64_t t0 = b * (int64_t)g.W + (odd ? g.W / 2 : 0) + (odd && !wide && b == g.nt - 1 ? g.X : 0);
+  const int64_t origin = t0 - g.R;
   const int64_t tl = left_tile(g, odd, b);
   const int64_t tr = right_tile(g, odd, b);
   const int per_level = g.C * 2 * g.R;
@@ -80,13 +98,21 @@ SW_HD void run_diamond(Cx& cx, const Geom& g_in, int64_t b, int odd, int mode, i
     const int k = rem % (2 * g.R);
     const int side = which == 0 ? 1 : 0;
     const int64_t tile = which == 0 ? tl : tr;
-    cx.load_edge(s & 1, cc, insert_pos(g, side, s, k), edge_index(g, tile, side, s, cc, k));
+    cx.load_edge(s & 1, cc, dofs + insert_pos(g, side, s, k), edge_index(g, tile, side, s, cc, k));
   });
+  if (wide) {
+    const int lo = odd ? g.R : g.R + g.W;
+    cx.for_range(0, g.X * g.C, [&](int i) {
+      const int cc = g.C == 1 ? 0 : i / g.X, k = i - cc * g.X;
+      cx.load_edge(g.h & 1, cc, lo + k, top_index(g, cc, k));
+    });
+  }
   cx.sync();
-  const int wall = window_wall(g, origin);
-  for (int s = 1; s <= hh; ++s) cx.level(s, 0, grow_lo(g, s), grow_hi(g, s), origin, wall);
+  const int wall = window_wall(g, origin, w + 2 * g.R);
+  for (int s = 1; s <= hh; ++s) cx.level(s, 0, dofs + grow_lo(g, s), dofs + grow_hi(g, s), origin, wall);
   if (mode == MODE_DIAMOND) {
-    for (int s = 1; s < g.h; ++s) cx.level(s, g.h, up_lo(g, s), up_hi(g, s), origin, wall);
+    const int top = wide ? g.h : g.h - 1;  // a triangle's tier h is empty; a wide tile's is its flat top
+    for (int s = 1; s <= top; ++s) cx.level(s, g.h, g.R + g.R * s, g.R + w - g.R * s, origin, wall);
     const int per_side_h = g.h * per_level;
     cx.for_range(0, 2 * per_side_h, [&](int i) {
       const int side = i >= per_side_h ? 1 : 0;
@@ -94,17 +120,24 @@ SW_HD void run_diamond(Cx& cx, const Geom& g_in, int64_t b, int odd, int mode, i
       const int s = rem / per_level;
       const int cc = (rem - s * per_level) / (2 * g.R);
       const int k = rem % (2 * g.R);
-      cx.store_edge(s & 1, cc, edge_pos(g, side, s, k), edge_index(g, b, side, s, cc, k));
+      cx.store_edge(s & 1, cc, edge_pos(g, side, s, k, w), edge_index(g, b, side, s, cc, k));
     });
+    if (wide) {
+      const int lo = g.R + g.W / 2;
+      cx.for_range(0, g.X * g.C, [&](int i) {
+        const int cc = g.C == 1 ? 0 : i / g.X, k = i - cc * g.X;
+        cx.store_edge(g.h & 1, cc, lo + k, top_index(g, cc, k));
+      });
+    }
   } else if (mode == MODE_DOWN) {
-    cx.for_range(0, g.W * g.C, [&](int i) {
-      const int cc = g.C == 1 ? 0 : i / g.W, k = i - cc * g.W;
+    cx.for_range(0, w * g.C, [&](int i) {
+      const int cc = g.C == 1 ? 0 : i / w, k = i - cc * w;
       cx.store_u(g.h & 1, cc, g.R + k, origin + g.R + k);
     });
   } else {
-    const int lo = grow_lo(g, hh), w = grow_hi(g, hh) - lo;
-    cx.for_range(0, w * g.C, [&](int i) {
-      const int cc = g.C == 1 ? 0 : i / w, k = i - cc * w;
+    const int lo = grow_lo(g, hh), gw = grow_hi(g, hh) - lo;
+    cx.for_range(0, gw * g.C, [&](int i) {
+      const int cc = g.C == 1 ? 0 : i / gw, k = i - cc * gw;
       cx.store_u(hh & 1, cc, lo + k, origin + lo + k);
     });
   }

@@ -46,7 +46,7 @@ class swept_plan_info(ctypes.Structure):
                 ("radius", ctypes.c_int32), ("stages", ctypes.c_int32), ("components", ctypes.c_int32),
                 ("tiles", ctypes.c_int64), ("smem_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
                 ("chunk", ctypes.c_int32), ("persistent", ctypes.c_int32), ("cluster", ctypes.c_int32),
-                ("warp_tiles", ctypes.c_int32)]
+                ("warp_tiles", ctypes.c_int32), ("last_tile_extra", ctypes.c_int32)]
 
 
 _H = ctypes.c_void_p
@@ -94,6 +94,7 @@ swept_batch_sizes = _sig("swept_batch_sizes", [_H, ctypes.POINTER(_I64), ctypes.
 swept_batch_bind_workspace = _sig("swept_batch_bind_workspace", [_H, _P, _SZ])
 swept_batch_set_option = _sig("swept_batch_set_option", [_H, _I32, _I64])
 swept_batch_run = _sig("swept_batch_run", [_H, _P, _P])
+swept_batch_run_classic = _sig("swept_batch_run_classic", [_H, _P, _P])
 swept_batch_sync_status = _sig("swept_batch_sync_status", [_H, _P])
 swept_batch_last_error = _sig("swept_batch_last_error", [_H, ctypes.c_char_p, _SZ])
 swept_batch_free = _sig("swept_batch_free", [_H], None)
@@ -312,8 +313,10 @@ def _swept_solve_fn():
 
         @staticmethod
         def backward(ctx, gT):
+            # the handle and its checkpoints stay alive with ctx (a second backward, as with
+            # retain_graph=True, continues from the same checkpoints); the Solver frees its
+            # handle when ctx is released
             g_u0, g_param = ctx.sol.adjoint(gT.contiguous(), ctx.nsteps, ctx.ckpt)
-            ctx.sol.close()
             gp = g_param.reshape(ctx.param_shape).to(ctx.param_device) if ctx.param_shape is not None else None
             return g_u0, gp, None, None
 
@@ -387,6 +390,14 @@ class Batch:
             raise ValueError("batch state must be a CUDA tensor of %d values of %s" % (self.state_values,
                                                                                       self.torch_dtype))
         self._check(swept_batch_run(self.b, ctypes.c_void_p(u.data_ptr()), _stream_ptr(stream)))
+        return u
+
+    def run_classic(self, u, stream=None):
+        """swept_batch_run_classic: the same advance with the classic decomposition."""
+        if not u.is_cuda or u.dtype != self.torch_dtype or u.numel() < self.state_values:
+            raise ValueError("batch state must be a CUDA tensor of %d values of %s" % (self.state_values,
+                                                                                      self.torch_dtype))
+        self._check(swept_batch_run_classic(self.b, ctypes.c_void_p(u.data_ptr()), _stream_ptr(stream)))
         return u
 
     def sync_status(self, stream=None):

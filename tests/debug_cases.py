@@ -3,7 +3,8 @@ test_debug_build.py in a child process, because a process loads one build.
 
 Every execution mode of every kernel family runs on small seeded cases:
   - heat, KS and Euler, per pass, persistent and cluster, in shared memory and
-    in warp tiles, periodic and insulated, with remainders;
+    in warp tiles, periodic and insulated, with remainders, and on grids that
+    are not a multiple of the tile width;
   - classic;
   - the batched solver, the adjoint, the no-allocation entry point;
   - 2D per pass and persistent, both boundary conditions.
@@ -92,6 +93,24 @@ def main():
             ref = oracle.euler(U0, pr["dx"], pr["dt"], pr["gamma"], nsteps, bc=bc, threads=8)
             run1d(S.EULER, code, U0, (pr["dx"], pr["dt"], pr["gamma"]), nsteps, ref, bc=bc, tile_w=W, **extra)
     clean("euler")
+
+    # grids that are not a multiple of the tile (wide last tile), per pass and persistent
+    for dtype in (np.float64, np.float32):
+        code = S.F64 if dtype == np.float64 else S.F32
+        for n, W, nsteps, bc, extra in [(1009, 64, 301, 0, {}), (1009, 32, 203, 1, {"persistent": 1}),
+                                        (2 * 64 + 63, 64, 77, 1, {})]:
+            p = inputs.heat_problem(n=n, dtype=dtype)
+            ref = oracle.heat(p["u0"], p["dx"], p["dt"], p["alpha"], nsteps, bc=bc)
+            run1d(S.HEAT, code, p["u0"], (p["dx"], p["dt"], p["alpha"]), nsteps, ref, bc=bc, tile_w=W, **extra)
+        for n, W, nsteps, extra in [(4099, 256, 155, {}), (1009, 64, 101, {"persistent": 1})]:
+            p = inputs.ks_problem(n=n, dtype=dtype)
+            ref = oracle.ks(p["u0"], p["dx"], p["dt"], p["nu"], nsteps, threads=8)
+            run1d(S.KS, code, p["u0"], (p["dx"], p["dt"], p["nu"]), nsteps, ref, tile_w=W, **extra)
+        for n, W, nsteps, extra in [(1009, 64, 99, {}), (2 * 128 + 1, 128, 71, {"persistent": 1})]:
+            pr = inputs.euler_problem(n=n, dtype=dtype)
+            ref = oracle.euler(pr["U0"], pr["dx"], pr["dt"], pr["gamma"], nsteps, bc=1, threads=8)
+            run1d(S.EULER, code, pr["U0"], (pr["dx"], pr["dt"], pr["gamma"]), nsteps, ref, bc=1, tile_w=W, **extra)
+    clean("ragged grids")
 
     # batched solver
     spec = inputs.batch_problems(count=24, seed=7, log2_lo=10, log2_hi=13, steps_lo=1, steps_hi=300)

@@ -187,6 +187,9 @@ def test_autotune_tile_candidates(S):
     # a non-power-of-two size keeps its legal divisors (multiples of 4r, >= 2 tiles)
     c = autotune.tile_candidates(S.KS, 3 * 1000)
     assert c and all(3000 % w == 0 and w % 8 == 0 and 3000 // w >= 2 for w in c)
+    # with no divisor, the powers of two that leave at least two tiles
+    assert autotune.tile_candidates(S.KS, 65537) == [64, 128, 256, 512, 1024]
+    assert autotune.tile_candidates(S.HEAT, 1009) == [32, 64, 128, 256]
 
 
 @pytest.mark.parametrize("scheme,W", [("heat", 32), ("heat", 64), ("heat", 256), ("ks", 64), ("ks", 128), ("ks", 256)])
@@ -262,6 +265,87 @@ def test_schedule_replay_random_configurations(S):
         assert S.swept_init(ctypes.byref(c), ctypes.byref(h_)) == S.SWEPT_OK
         assert S.check_schedule(h_.value, nsteps) == nt * W * nsteps * S_, (scheme, W, nt, bc, nsteps)
         S.swept_free(h_.value)
+
+
+def test_schedule_replay_ragged_grids(S):
+    """Grids that are not a multiple of the tile width (the last tile wider by
+    X = n mod W, its flat top handed from pass to pass): seeded sweep of both
+    replays (launch sequence and persistent queue) over schemes, boundaries,
+    tile widths, X in [1, W), tile counts and step counts."""
+    import numpy as np
+
+    g = np.random.default_rng(1009)
+    for _ in range(80):
+        scheme = int(g.integers(0, 3))
+        R = 1 if scheme == S.HEAT else 2
+        W = 4 * R * int(g.integers(1, 7))
+        nt = int(g.integers(2, 8))
+        X = int(g.integers(1, W))
+        n = nt * W + X
+        bc = 0 if scheme == S.KS else int(g.integers(0, 2))
+        S_ = 1 if scheme == S.HEAT else 2
+        h = W // (2 * R)
+        nsteps = int(g.choice([1, max(1, h // S_), int(g.integers(1, 5 * h))]))
+        for persistent in (0, 1):
+            c = cfg(S, scheme=scheme, n=n, tile_w=W, bc=bc, param0=1.4 if scheme == S.EULER else 1.0,
+                    persistent=persistent)
+            hh = ctypes.c_void_p()
+            assert S.swept_init(ctypes.byref(c), ctypes.byref(hh)) == S.SWEPT_OK
+            p = S.plan(hh.value)
+            assert (p["tiles"], p["last_tile_extra"]) == (nt, X)
+            k = ctypes.c_int64()
+            st = S.swept_check_schedule(hh.value, nsteps, ctypes.byref(k))
+            assert st == S.SWEPT_OK, (S.last_error(hh.value), scheme, W, nt, X, bc, nsteps, persistent)
+            assert k.value == n * nsteps * S_
+            S.swept_free(hh.value)
+
+
+@pytest.mark.parametrize("n", [1009, 4099, 65537])
+@pytest.mark.parametrize("scheme,bc", [("heat", 0), ("heat", 1), ("ks", 0), ("euler", 0), ("euler", 1)])
+def test_schedule_replay_prime_grids(S, n, scheme, bc):
+    """The ragged sizes of the GPU parity tests, with the library's default
+    tile and with a 64-point tile in the persistent queue: both replays pass."""
+    sc = {"heat": S.HEAT, "ks": S.KS, "euler": S.EULER}[scheme]
+    S_ = 1 if sc == S.HEAT else 2
+    param = 1.4 if sc == S.EULER else 1.0
+    for W, persistent, nsteps in ((0, 0, 77), (64, 0, 203), (64 if n < 5000 else 1024, 1, 41)):
+        h = S.init(cfg(S, scheme=sc, n=n, tile_w=W, bc=bc, param0=param, persistent=persistent))
+        p = S.plan(h)
+        assert p["tiles"] * p["tile_w"] + p["last_tile_extra"] == n and p["last_tile_extra"] > 0
+        assert S.check_schedule(h, nsteps) == n * nsteps * S_
+        S.swept_free(h)
+
+
+def test_default_tile_prefers_a_divisor(S):
+    """The library keeps a tile that divides n when one exists (no wide tile)."""
+    for n in (1 << 14, 3 * 1000, 1 << 20):
+        p = S.plan(S.init(cfg(S, n=n)))
+        assert p["last_tile_extra"] == 0 and n % p["tile_w"] == 0
+
+
+@pytest.mark.parametrize("scheme,n", [("heat", 3), ("heat", 7), ("ks", 5), ("ks", 15), ("euler", 5), ("euler", 15)])
+def test_tiny_grids_get_a_classic_only_handle(S, scheme, n):
+    """Any n >= 2r + 1 is a valid problem; below two tiles of 4r points the
+    handle exists for classic_step_n, and the swept calls say so."""
+    sc = {"heat": S.HEAT, "ks": S.KS, "euler": S.EULER}[scheme]
+    c = cfg(S, scheme=sc, n=n, param0=1.4 if sc == S.EULER else 1.0, bc=1 if sc == S.EULER else 0)
+    h = S.init(c)
+    assert S.plan(h)["tiles"] == 0
+    assert S.swept_check_schedule(h, 3, None) == S.SWEPT_EUNSUPPORTED
+    S.swept_free(h)
+    bad = cfg(S, scheme=sc, n=2 * (1 if sc == S.HEAT else 2), param0=1.4 if sc == S.EULER else 1.0)
+    hb = ctypes.c_void_p()
+    assert S.swept_init(ctypes.byref(bad), ctypes.byref(hb)) == S.SWEPT_EINVAL
+    for extra in (dict(persistent=1), dict(cluster=1), dict(tile_w=8 if sc == S.HEAT else 16)):
+        c2 = cfg(S, scheme=sc, n=n, param0=1.4 if sc == S.EULER else 1.0, **extra)
+        assert S.swept_init(ctypes.byref(c2), ctypes.byref(hb)) == S.SWEPT_EINVAL, extra
+
+
+def test_ragged_grids_refuse_cluster_and_warp_tiles(S):
+    for extra in (dict(cluster=1, tile_w=64), dict(warp_tiles=1, tile_w=64)):
+        c = cfg(S, n=3 * 64 + 8, **extra)
+        h = ctypes.c_void_p()
+        assert S.swept_init(ctypes.byref(c), ctypes.byref(h)) == S.SWEPT_EINVAL, extra
 
 
 @pytest.mark.parametrize("option,value", [(0, 5), (3, 1), (1, 0), (1, 1 << 33), (2, -1)])

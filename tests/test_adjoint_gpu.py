@@ -174,3 +174,38 @@ def test_autograd_function(S):
     ref, ref_nu, cond = oracle.ks_adjoint(p["u0"], p["dx"], p["dt"], 1.0, nsteps, gT, with_condition=True)
     assert np.array_equal(u0.grad.cpu().numpy(), ref)
     assert abs(float(nu.grad) - ref_nu) <= param_tol(ref_nu, cond)
+
+
+def test_autograd_second_backward_with_retained_graph(S):
+    """backward twice through a retained graph: the handle and its checkpoints
+    stay alive with the autograd context, and both gradients equal the oracle's."""
+    import torch
+
+    n, nsteps = 512, 150
+    p = inputs.ks_problem(n=n, seed=93)
+    u0 = torch.from_numpy(p["u0"]).cuda().requires_grad_(True)
+    nu = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    target = torch.from_numpy(inputs.rng(94).standard_normal(n)).cuda()
+    uT = S.SweptSolve.apply(u0, nu, nsteps, dx=p["dx"], dt=p["dt"], tile_w=64)
+    loss = ((uT - target) ** 2).sum()
+    loss.backward(retain_graph=True)
+    g1 = u0.grad.clone()
+    u0.grad = None
+    loss.backward()
+    ref_uT = oracle.ks(p["u0"], p["dx"], p["dt"], 1.0, nsteps)
+    ref = oracle.ks_adjoint(p["u0"], p["dx"], p["dt"], 1.0, nsteps, 2 * (ref_uT - target.cpu().numpy()))[0]
+    assert np.array_equal(g1.cpu().numpy(), ref)
+    assert np.array_equal(u0.grad.cpu().numpy(), ref)
+
+
+def test_default_checkpoint_memory_is_the_smallest_layout(S):
+    """swept_adjoint_ckpt_size gives the segment length with the least memory:
+    at the adjoint workload's size (KS 2^18, 5,000 steps, tile 512: 64 steps per
+    pass) that is one pass per segment, 79 checkpoints plus a 129-tier tape."""
+    n = 1 << 18
+    sol = S.Solver(S.KS, S.F64, n, 0.785, 0.005, 1.0, tile_w=512)
+    nb = sol.ckpt_size(5000)
+    sol.close()
+    state = n * 8
+    assert nb < (79 + 129 + 3) * state + (1 << 16), nb
+    assert nb > (79 + 129) * state

@@ -9,6 +9,8 @@ workspace, advanced the same way.  It must pass alone in a fresh process and
 after every other test (the array keeps the previous call's contents).
 """
 import ctypes
+import os
+import re
 
 import numpy as np
 import pytest
@@ -16,6 +18,24 @@ import pytest
 from paper_1612_02495_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
+
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def scratch_bytes():
+    """SWEPT_STATIC_SCRATCH_BYTES as include/swept.h defines it."""
+    text = open(os.path.join(ROOT, "include", "swept.h")).read()
+    m = re.search(r"#define\s+SWEPT_STATIC_SCRATCH_BYTES\s+\((\d+)u\s*<<\s*(\d+)\)", text)
+    return int(m.group(1)) << int(m.group(2))
+
+
+def largest_fp64_ks_grid():
+    """The largest power-of-two FP64 KS grid whose two edge buffers (2 n values each) fit the array."""
+    n = 1
+    while 4 * (2 * n) * 8 <= scratch_bytes():
+        n *= 2
+    return n
 
 
 @pytest.fixture(scope="module")
@@ -72,10 +92,61 @@ def test_static_scratch_matches_workspace_entry(S, kind, dtype, n, W, calls):
     ref.close()
 
 
+def test_static_scratch_accepts_the_largest_grid_that_fits(S):
+    """n = 2^18 FP64 KS needs 4 * n * 8 bytes = the whole array: accepted, and
+    equal to swept_step_n."""
+    import torch
+
+    n = largest_fp64_ks_grid()
+    assert 4 * n * 8 == scratch_bytes()
+    p = inputs.ks_problem(n=n)
+    cfg = S.make_config(S.KS, S.F64, n, p["dx"], p["dt"], p["nu"], tile_w=1024)
+    a = torch.from_numpy(p["u0"]).cuda()
+    b = a.clone()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert S.swept_step_n_static(ctypes.byref(cfg), ctypes.c_void_p(a.data_ptr()), 300, stream) == S.SWEPT_OK
+    ref = S.Solver(S.KS, S.F64, n, p["dx"], p["dt"], p["nu"], tile_w=1024)
+    ref.step(b, 300)
+    torch.cuda.synchronize()
+    ref.close()
+    assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
+
+
+def test_static_scratch_large_tile_keeps_a_handles_opt_in(S):
+    """A static call whose tile needs more than 48 KB of shared memory (Euler
+    FP64, tile 512: about 50 KB), made between two solves of a handle with a
+    larger tile (tile 1024: about 99 KB), must not lower the kernels' opt-in
+    limit: the handle's next solve (a fresh graph capture) still succeeds and
+    every result equals classic."""
+    import torch
+
+    n = 1 << 16
+    p = inputs.euler_problem(n=n)
+    big = S.Solver(S.EULER, S.F64, n, p["dx"], p["dt"], p["gamma"], bc=S.BC_REFLECTIVE, tile_w=1024)
+    assert big.plan["smem_bytes"] > 96 * 1024
+    a = torch.from_numpy(p["U0"]).cuda()
+    ref = a.clone()
+    big.step(a, 40)
+    big.classic(ref, 40)
+    cfg = S.make_config(S.EULER, S.F64, n, p["dx"], p["dt"], p["gamma"], bc=S.BC_REFLECTIVE, tile_w=512)
+    c = torch.from_numpy(p["U0"]).cuda()
+    c_ref = c.clone()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert S.swept_step_n_static(ctypes.byref(cfg), ctypes.c_void_p(c.data_ptr()), 57, stream) == S.SWEPT_OK
+    big.classic(c_ref, 57)
+    big.step(a, 23)  # a new step count: a new capture of the 99 KB kernels
+    big.classic(ref, 23)
+    torch.cuda.synchronize()
+    big.sync_status()
+    big.close()
+    assert np.array_equal(c.cpu().numpy(), c_ref.cpu().numpy())
+    assert np.array_equal(a.cpu().numpy(), ref.cpu().numpy())
+
+
 def test_static_scratch_rejects_grids_beyond_its_size(S):
     import torch
 
-    n = 1 << 19  # FP64 KS needs 4 * n * 8 bytes = 16 MiB > 8 MiB
+    n = 2 * largest_fp64_ks_grid()  # FP64 KS needs 4 * n * 8 bytes = twice the array
     p = inputs.ks_problem(n=n)
     cfg = S.make_config(S.KS, S.F64, n, p["dx"], p["dt"], p["nu"], tile_w=1024)
     u = torch.from_numpy(p["u0"]).cuda()
