@@ -352,7 +352,7 @@ swept_status swept_init(const swept_config* cfg, swept_handle** out) {
     g.h = W / (2 * R);
     g.nt = cfg->n / W;
     g.X = (int)(cfg->n - g.nt * W);
-    g.M = W + g.X + 2 * R;
+    g.M = (W + g.X + 2 * R + 1) / 2 * 2;  // even row stride: paired (8- / 16-byte) loads stay aligned
     g.E = 2 * g.h * g.C * 2 * R;
   }
   // one point per thread per tier unless asked: on GB300 the register-window

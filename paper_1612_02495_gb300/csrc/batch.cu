@@ -30,6 +30,7 @@
 
 #include "debug_check.cuh"
 #include "impl.h"
+#include "kernels.cuh"
 #include "ops.cuh"
 #include "swept.h"
 #include "trace.h"
@@ -97,27 +98,10 @@ struct BatchCtx {
   __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) {
     if (dbg::win(g.M, r, c, kC, j) && dbg::in_range(e, edge_slots(g) * g.E, dbg::EDGE)) e_out[e] = row(r, c)[j];
   }
+  // the per-problem kernels' tier code (strided, or paired for radius 2)
   __device__ __forceinline__ void level(int s, int, int lo, int hi, int64_t, int wall) {
-    if (!dbg::level(g.M, lo, hi, kR))
-      ;
-    else if (stage_c<Op>(s) == 0)
-      scalar_tier<0>(lo, hi, s & 1, wall);
-    else
-      scalar_tier<1>(lo, hi, s & 1, wall);
+    if (dbg::level(g.M, lo, hi, kR)) LevelImpl<T, Op>::run(sm, g.M, stage_c<Op>(s), s & 1, lo, hi, wall, 1, k);
     __syncthreads();
-  }
-  template <int STAGE>
-  __device__ __forceinline__ void scalar_tier(int lo, int hi, int out_row, int wall) {
-    constexpr int R = Op::R;
-    const T* in = sm + (out_row ^ 1) * g.M;
-    T* out = sm + out_row * g.M;
-    for (int j = lo + (int)threadIdx.x; j < hi; j += (int)blockDim.x) {
-      T v[2 * R + 1];
-#pragma unroll
-      for (int d = 0; d <= 2 * R; ++d) v[d] = in[nbr(j, d - R, wall)];
-      const T p2 = STAGE == 1 ? out[j] : T(0);
-      out[j] = Op::template point<STAGE>(v, p2, k);
-    }
   }
 };
 

@@ -32,27 +32,49 @@ struct Launch {
     }
     return cudaErrorInvalidValue;
   }
+  // Euler's shared-memory-tier kernels also exist with 256-thread launch bounds
+  // (more registers a thread, no spills), used whenever a block has <= 256 threads
+  static constexpr bool kSmallBlockVariant = Op::C == 3;
+  static bool small_block(int P, int threads) { return kSmallBlockVariant && P == 0 && threads <= 256; }
+  // fn(std::integral_constant<int, MAXT>) for the launch-bounds variant of (P, threads)
+  template <class Fn>
+  static cudaError_t with_maxt(int P, int threads, Fn&& fn) {
+    if constexpr (kSmallBlockVariant) {
+      if (small_block(P, threads)) return fn(std::integral_constant<int, 256>{});
+    }
+    return fn(std::integral_constant<int, 1024>{});
+  }
   static cudaError_t prepare(size_t bytes) {
     cudaError_t e = raise_smem_limit((const void*)k_swept_up<T, Op>, bytes);
-    if (e != cudaSuccess) return e;
-    return raise_smem_limit((const void*)k_swept_diamond<T, Op>, bytes);
+    if (e == cudaSuccess) e = raise_smem_limit((const void*)k_swept_diamond<T, Op>, bytes);
+    if constexpr (kSmallBlockVariant) {
+      if (e == cudaSuccess) e = raise_smem_limit((const void*)k_swept_up<T, Op, 0, 256>, bytes);
+      if (e == cudaSuccess) e = raise_smem_limit((const void*)k_swept_diamond<T, Op, 0, 256>, bytes);
+    }
+    return e;
   }
   static cudaError_t up(const Geom& g, const void* k, const void* u_in, void* u_out, void* e_out, int hh,
                         int write_top, int threads, size_t smem, cudaStream_t s) {
     return with_p(g.P, [&](auto pc) {
       constexpr int P = decltype(pc)::value;
-      k_swept_up<T, Op, P><<<(unsigned)g.nt, threads, smem, s>>>(g, kc(k), (const T*)u_in, (T*)u_out, (T*)e_out, hh,
-                                                                 write_top);
-      return cudaGetLastError();
+      return with_maxt(P, threads, [&](auto mc) {
+        constexpr int MAXT = decltype(mc)::value;
+        k_swept_up<T, Op, P, MAXT><<<(unsigned)g.nt, threads, smem, s>>>(g, kc(k), (const T*)u_in, (T*)u_out,
+                                                                         (T*)e_out, hh, write_top);
+        return cudaGetLastError();
+      });
     });
   }
   static cudaError_t diamond(const Geom& g, const void* k, void* u_out, const void* e_in, void* e_out, int odd,
                              int mode, int hh, int threads, size_t smem, cudaStream_t s) {
     return with_p(g.P, [&](auto pc) {
       constexpr int P = decltype(pc)::value;
-      k_swept_diamond<T, Op, P><<<(unsigned)g.nt, threads, smem, s>>>(g, kc(k), (T*)u_out, (const T*)e_in,
-                                                                      (T*)e_out, odd, mode, hh);
-      return cudaGetLastError();
+      return with_maxt(P, threads, [&](auto mc) {
+        constexpr int MAXT = decltype(mc)::value;
+        k_swept_diamond<T, Op, P, MAXT><<<(unsigned)g.nt, threads, smem, s>>>(g, kc(k), (T*)u_out, (const T*)e_in,
+                                                                              (T*)e_out, odd, mode, hh);
+        return cudaGetLastError();
+      });
     });
   }
   static cudaError_t classic(const Geom& g, const void* k, int stage, const void* in, void* out, cudaStream_t s) {
@@ -73,20 +95,26 @@ struct Launch {
                              int blocks, int threads, size_t smem, cudaStream_t s) {
     return with_p(g.P, [&](auto pc) {
       constexpr int P = decltype(pc)::value;
-      cudaError_t e = raise_smem_limit((const void*)k_swept_persist<T, Op, P>, smem);
-      if (e != cudaSuccess) return e;
-      PersistCtl c{done, queue, error, spin_limit, start_item};
-      k_swept_persist<T, Op, P><<<blocks, threads, smem, s>>>(g, kc(k), (T*)u, (T*)e0, (T*)e1, n_sub, c);
-      return cudaGetLastError();
+      return with_maxt(P, threads, [&](auto mc) {
+        constexpr int MAXT = decltype(mc)::value;
+        cudaError_t e = raise_smem_limit((const void*)k_swept_persist<T, Op, P, MAXT>, smem);
+        if (e != cudaSuccess) return e;
+        PersistCtl c{done, queue, error, spin_limit, start_item};
+        k_swept_persist<T, Op, P, MAXT><<<blocks, threads, smem, s>>>(g, kc(k), (T*)u, (T*)e0, (T*)e1, n_sub, c);
+        return cudaGetLastError();
+      });
     });
   }
   static int persist_blocks_per_sm(int P_, int threads, size_t smem) {
     int n = 0;
     const cudaError_t e = with_p(P_, [&](auto pc) {
       constexpr int P = decltype(pc)::value;
-      cudaError_t e2 = raise_smem_limit((const void*)k_swept_persist<T, Op, P>, smem);
-      if (e2 != cudaSuccess) return e2;
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_swept_persist<T, Op, P>, threads, smem);
+      return with_maxt(P, threads, [&](auto mc) {
+        constexpr int MAXT = decltype(mc)::value;
+        cudaError_t e2 = raise_smem_limit((const void*)k_swept_persist<T, Op, P, MAXT>, smem);
+        if (e2 != cudaSuccess) return e2;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_swept_persist<T, Op, P, MAXT>, threads, smem);
+      });
     });
     return e == cudaSuccess ? n : 0;
   }

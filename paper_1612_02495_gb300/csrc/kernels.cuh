@@ -108,9 +108,52 @@ __device__ __forceinline__ void strided2_level(T* sm, int M, int out_row, int lo
   }
 }
 
+// Radius-2 tier with each thread advancing the aligned pair (j, j + 1), j
+// even: its six inputs j-2 .. j+3 come from three paired loads (float2) and
+// both results go out in one paired store, 2.25 shared-memory instructions a
+// point instead of 6.5.  Needs even lo and hi and an even row
+// stride (every KS tier of a tile whose width is a multiple of 8 has even
+// bounds).  Each point is the same Op::point on the same operands.
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+  using type = float2;
+};
+template <>
+struct Pair<double> {
+  using type = double2;
+};
+
+template <typename T, class Op, int STAGE>
+__device__ __forceinline__ void paired_level(T* sm, int M, int out_row, int lo, int hi, const typename Op::K& k) {
+  static_assert(Op::R == 2, "paired tiers are for radius-2 stencils");
+  using T2 = typename Pair<T>::type;
+  const T2* in = reinterpret_cast<const T2*>(sm + (out_row ^ 1) * M);
+  T2* out = reinterpret_cast<T2*>(sm + out_row * M);
+  for (int jp = (lo >> 1) + (int)threadIdx.x; jp < (hi >> 1); jp += (int)blockDim.x) {
+    const T2 a = in[jp - 1], b = in[jp], c = in[jp + 1];
+    const T v[6] = {a.x, a.y, b.x, b.y, c.x, c.y};
+    const T2 p2 = STAGE == 1 ? out[jp] : T2{T(0), T(0)};
+    T2 r;
+    r.x = Op::template point<STAGE>(&v[0], p2.x, k);
+    r.y = Op::template point<STAGE>(&v[1], p2.y, k);
+    out[jp] = r;
+  }
+}
+
 template <typename T, class Op, int STAGE>
 __device__ __forceinline__ void scalar_level_any(T* sm, int M, int out_row, int lo, int hi, int wall, int chunk,
                                                  const typename Op::K& k) {
+  // FP32 only: in FP64 a warp instruction holds the FP64 pipe for 64 cycles
+  // whatever its active lanes, and pairs double the partial-warp waste at the
+  // triangle tips (measured 4 % slower on the FP64 KS workload)
+  if constexpr (Op::R == 2 && sizeof(T) == 4) {
+    if (wall == NO_WALL && chunk <= 1 && ((lo | hi | M) & 1) == 0) {
+      paired_level<T, Op, STAGE>(sm, M, out_row, lo, hi, k);
+      return;
+    }
+  }
   if (wall != NO_WALL || chunk <= 1) {
     scalar_level<T, Op, STAGE>(sm, M, out_row, lo, hi, wall, k);
     return;
@@ -239,7 +282,14 @@ __device__ __forceinline__ void euler_level(T* sm, int M, int out_row, int lo, i
   // handed to its own thread so the wall costs no thread a second flux.
   const int nf = hi - lo + 1;
   const int nitems = nf + ((wall != NO_WALL && wall >= lo && wall <= hi) ? 1 : 0);
-  if (!PAIR) {
+  if (!PAIR && wall == NO_WALL) {
+    // no wall in the window: faces read their four cells directly
+    for (int f = lo + (int)threadIdx.x; f <= hi; f += (int)blockDim.x) {
+      const typename EulerOp<T>::Prim a{pr[f - 2], pu[f - 2], pp[f - 2]}, b{pr[f - 1], pu[f - 1], pp[f - 1]},
+          c{pr[f], pu[f], pp[f]}, d{pr[f + 1], pu[f + 1], pp[f + 1]};
+      EulerOp<T>::flux(a, b, c, d, k, F0[f], F1[f], F2[f]);
+    }
+  } else if (!PAIR) {
     for (int i = (int)threadIdx.x; i < nitems; i += (int)blockDim.x) {
       if (i < nf) {
         const int f = lo + i;
@@ -362,7 +412,9 @@ struct DevCtx {
   __device__ __forceinline__ void level(int s, int base, int lo, int hi, int64_t origin, int wall) {
     if (dbg::level(g.M, lo, hi, kR)) LevelImpl<T, Op>::run(sm, g.M, stage_c<Op>(s), s & 1, lo, hi, wall, g.chunk, k);
     if (TAPE) {
-      // each thread stores the values it computed itself, so no barrier is needed first
+      // the tier's mapping of points to threads (strided, paired or chunked)
+      // need not match this loop's, so the tier must be complete first
+      __syncthreads();
       const int64_t slot = tape.base + base + s - tape.tier0;
       if (slot >= 0 && slot < tape.ntiers)
         for (int j = lo + (int)threadIdx.x; j < hi; j += (int)blockDim.x) {
@@ -507,6 +559,13 @@ __device__ __forceinline__ typename WithTiers<Base, P>::type tiers_ctx(const Bas
   return typename WithTiers<Base, P>::type(base);
 }
 
+// Launch bounds of the swept kernels.  P > 0: one warp per block, 16 blocks
+// per SM.  Shared-memory tiers: MAXT threads at most; MAXT = 1024 caps a
+// thread at 64 registers; MAXT = 256 (the variant Euler runs with up to 256
+// threads) at 85 with 3 blocks per SM, which measured faster on the Euler
+// workloads than 2 blocks of up to 128 registers.
+#define SWEPT_BOUNDS(P, MAXT) __launch_bounds__((P) > 0 ? 32 : (MAXT), (P) > 0 ? 16 : ((MAXT) <= 256 ? 3 : 1))
+
 // ---------------------------------------------------------------------------
 // persistent single-problem swept kernel: the launch sequence of
 // for_each_launch as one queue of (pass k, tile b) items, item = k * nt + b,
@@ -571,8 +630,8 @@ __device__ __forceinline__ bool persist_wait(const int* flag, int need, const Pe
   }
 }
 
-template <typename T, class Op, int P = 0>
-__global__ void __launch_bounds__(P > 0 ? 32 : 1024, P > 0 ? 16 : 1) k_swept_persist(Geom g, typename Op::K k, T* u, T* e0, T* e1, int64_t n_sub,
+template <typename T, class Op, int P = 0, int MAXT = 1024>
+__global__ void SWEPT_BOUNDS(P, MAXT) k_swept_persist(Geom g, typename Op::K k, T* u, T* e0, T* e1, int64_t n_sub,
                                                         PersistCtl ctl) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int64_t s_item;
@@ -713,16 +772,16 @@ static __global__ void k_latch_error(const int* err, int* status) {
   if (threadIdx.x == 0 && blockIdx.x == 0 && *err != 0 && *status == 0) *status = *err;
 }
 
-template <typename T, class Op, int P = 0>
-__global__ void __launch_bounds__(P > 0 ? 32 : 1024, P > 0 ? 16 : 1) k_swept_up(Geom g, typename Op::K k, const T* u_in, T* u_out, T* e_out,
+template <typename T, class Op, int P = 0, int MAXT = 1024>
+__global__ void SWEPT_BOUNDS(P, MAXT) k_swept_up(Geom g, typename Op::K k, const T* u_in, T* u_out, T* e_out,
                                                    int hh, int write_top) {
   extern __shared__ __align__(16) unsigned char smraw[];
   auto cx = tiers_ctx<P>(DevCtx<T, Op>{reinterpret_cast<T*>(smraw), g, k, u_in, u_out, nullptr, e_out, Tape<T>{}});
   run_up(cx, g, (int64_t)blockIdx.x, hh, write_top != 0);
 }
 
-template <typename T, class Op, int P = 0>
-__global__ void __launch_bounds__(P > 0 ? 32 : 1024, P > 0 ? 16 : 1) k_swept_diamond(Geom g, typename Op::K k, T* u_out, const T* e_in, T* e_out,
+template <typename T, class Op, int P = 0, int MAXT = 1024>
+__global__ void SWEPT_BOUNDS(P, MAXT) k_swept_diamond(Geom g, typename Op::K k, T* u_out, const T* e_in, T* e_out,
                                                         int odd, int mode, int hh) {
   extern __shared__ __align__(16) unsigned char smraw[];
   auto cx = tiers_ctx<P>(DevCtx<T, Op>{reinterpret_cast<T*>(smraw), g, k, nullptr, u_out, e_in, e_out, Tape<T>{}});
