@@ -52,6 +52,77 @@ PERSIST_TRAFFIC_BYTES = 48860000
 PERSIST_TRAFFIC_PLAN = (1024, 512)  # (tile, threads) of that capture
 
 
+# Measured unit ceilings of GB300 (python -m paper_1612_02495_gb300.peaks, register-only probe loops):
+# FP32 FMA 3.917e13/s (2 flops each), conflict-free 32-bit shared-memory loads 3.908e13 B/s.
+FP32_PEAK_TFLOPS = 2 * 3.917e13 / 1e12
+SMEM_PEAK_GBS = 3.908e13 / 1e9
+# Algorithmic work per point-substep, counted from the per-point operators (ops.cuh; the 2D
+# heat operator in swept2d.cuh): FP instructions (add, mul, fma; div and sqrt one each), flops
+# (fma = 2) and shared-memory accesses per point of a tier in shared memory (stencil loads, the
+# second stage's read of the point's own earlier tier, the store).  Euler per cell-substep:
+# primitives (2 mul, 1 fma, 1 div), a face flux (2 sides x (12 reconstruction ops, 4 for
+# momentum and energy, 1 mul, 1 div, 1 sqrt, 1 add) + 18 for the Rusanov flux), the update of
+# 3 components (avg. 9 ops over the two stages).
+# FP32 KS tiers advance aligned pairs of points (three paired loads and one paired store per
+# pair, plus the second stage's paired read of the points' own earlier tier): 4.5 values a point.
+WORK = {
+    "heat": {"instr": 3, "flops": 4, "smem_acc": 4.0},
+    "ks": {"instr": 11, "flops": 18, "smem_acc": 6.5, "smem_acc_paired_f32": 4.5},
+    "euler": {"instr": 71, "flops": 82, "smem_acc": 34.5},
+    "heat2d": {"instr": 5, "flops": 6, "smem_acc": 6.0},
+}
+
+
+def alu_roofline(scheme, f64, units, ms, kernel, registers=False, note=None):
+    """Roofline of a swept kernel that did `units` point-substeps in `ms`: FP pipe
+    (flops against the FP64 or FP32 roof) and shared memory (algorithmic accesses
+    of the shared-memory tiers against the probed bandwidth; tiers in registers
+    touch shared memory only at pass boundaries)."""
+    w = WORK[scheme]
+    rate = units / (ms * 1e-3)
+    peak = FP64_PEAK_TFLOPS if f64 else FP32_PEAK_TFLOPS
+    achieved = w["flops"] * rate / 1e12
+    vb = 8 if f64 else 4
+    acc = w["smem_acc"] if f64 else w.get("smem_acc_paired_f32", w["smem_acc"])
+    smem_gbs = 0.0 if registers else acc * vb * rate / 1e9
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+           "traffic": None, "kernel": kernel, "kernel_ms": ms, "units": units,
+           "peak_source": ("derived FP64 roof: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz" if f64 else
+                           "measured FP32 FMA rate x 2 flop (probe)"),
+           "algorithmic_per_unit": {"flops": w["flops"], "fp_instr": w["instr"],
+                                    "smem_bytes": 0 if registers else acc * vb},
+           "smem": {"achieved": smem_gbs, "peak": SMEM_PEAK_GBS, "unit": "GB/s", "frac": smem_gbs / SMEM_PEAK_GBS,
+                    "peak_source": "measured conflict-free shared-memory loads (probe)"}}
+    if registers:
+        out["smem"]["note"] = "tiers in registers (warp tiles): shared memory only at pass boundaries"
+    if note:
+        out["note"] = note
+    return out
+
+
+def dominant_swept_kernel(sol, u, u0, nsteps, solve_ms):
+    """(kernel name, point-substeps per launch, average launch ms, share) of the
+    dominant kernel of a tuned 1D plan: the persistent or cluster kernel is one
+    launch per solve (timed by the solve's CUDA events); per-pass plans time the
+    diamond launches with CUDA events around each (swept_profile_passes)."""
+    plan = sol.plan
+    units = sol.n * plan["stages"] * nsteps
+    P = plan["tile_w"] // 32 if plan.get("warp_tiles") else 0
+    tmpl = "<%s, %s%s>" % ("double" if sol.dtype == 1 else "float",
+                          {0: "HeatOp", 1: "KsOp", 2: "EulerOp"}[sol.scheme], ", %d" % P if P else "")
+    if plan.get("persistent"):
+        return "k_swept_persist" + tmpl, units, solve_ms, 1.0
+    if plan.get("cluster"):
+        return "k_swept_cluster" + tmpl, units, solve_ms, 1.0
+    u.copy_(u0)
+    prof = sol.profile_passes(u, nsteps)
+    d_ms, d_n = prof["diamond"]
+    total = max(sum(v[0] for v in prof.values()), 1e-9)
+    if d_n == 0:
+        return "all swept passes" + tmpl, units, total, 1.0
+    return "k_swept_diamond" + tmpl, sol.n * plan["half_cycle"], d_ms / d_n, d_ms / total
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -225,13 +296,16 @@ def measure_fp32(S, inputs, autotune, torch, stream, barrier, ws):
             ms.append(ev[0].elapsed_time(ev[1]))
         res[name] = min(ms)
     sol.sync_status()
+    kname, kunits, kms, share = dominant_swept_kernel(sol, u, u0, NSTEPS, res["swept"])
     sol.close()
+    rf = alu_roofline("ks", False, kunits, kms, kname, registers=bool(t.get("warp_tiles")))
+    rf["kernel_share"] = share
     return {"workload": "KS N=2^20 FP32, 50,000 steps", "tile_w": t["tile_w"], "threads": t["threads"],
             "plan": {k: t.get(k, 0) for k in ("tile_w", "threads", "warp_tiles", "persistent", "cluster")},
             "swept_ms": res["swept"], "classic_ms": res["classic"],
             "swept_value": ws * N * NSTEPS / (res["swept"] * 1e-3),
             "classic_value": ws * N * NSTEPS / (res["classic"] * 1e-3),
-            "speedup_vs_classic": res["classic"] / res["swept"]}
+            "speedup_vs_classic": res["classic"] / res["swept"], "roofline": rf}
 
 
 def measure_batch(S, inputs, autotune, torch, stream, barrier, ws, with_f64):
@@ -241,6 +315,12 @@ def measure_batch(S, inputs, autotune, torch, stream, barrier, ws, with_f64):
     work = int((spec["n"] * spec["steps"]).sum())
     out = {"workload": "4096 problems, N=2^U(10,18) (multiples of 1024), heat/KS 50/50, steps U{1000..20000}",
            "cell_updates": work}
+    # point-substeps and flops of the whole batch (heat: 1 sub-step per step, KS: 2)
+    heat = spec["kind"] == 0
+    units = int((spec["n"] * spec["steps"] * np.where(heat, 1, 2)).sum())
+    flops = float((spec["n"] * spec["steps"] * np.where(heat, WORK["heat"]["flops"], 2 * WORK["ks"]["flops"])).sum())
+    smem_ks = {True: WORK["ks"]["smem_acc"], False: WORK["ks"]["smem_acc_paired_f32"]}
+    # FP64 takes about 50 s per run: one timed run each (its graph is captured on a short warm-up batch)
     for dt, code, name, runs in ((np.float32, S.F32, "f32", 2), (np.float64, S.F64, "f64", 1)):
         if code == S.F64 and not with_f64:
             continue
@@ -249,17 +329,33 @@ def measure_batch(S, inputs, autotune, torch, stream, barrier, ws, with_f64):
         b = S.Batch(autotune.apply_batch_plan(probs, plan), code, threads=plan["threads"])
         u0 = b.pack([q["u0"] for q in probs])
         u = u0.clone()
-        b.run(u)
-        barrier()
-        ms = []
-        for _ in range(runs):
-            u.copy_(u0)
-            ev = _event_time(torch, stream, lambda: b.run(u))
-            barrier()
-            ms.append(ev[0].elapsed_time(ev[1]))
+        res = {}
+        for kind, fn in (("swept", b.run), ("classic", b.run_classic)):
+            if runs > 1:
+                fn(u)  # warm-up: captures the graphs
+                barrier()
+            ms = []
+            for _ in range(runs):
+                u.copy_(u0)
+                ev = _event_time(torch, stream, lambda: fn(u))
+                barrier()
+                ms.append(ev[0].elapsed_time(ev[1]))
+            res[kind] = min(ms)
         b.sync_status()
-        out[name] = {"ms": min(ms), "value": ws * work / (min(ms) * 1e-3), "unit": UNIT, "tile_w": plan["tile_w"],
-                     "threads": plan["threads"], "items": b.items}
+        f64 = code == S.F64
+        rf = alu_roofline("ks", f64, units, res["swept"], "k_batch<%s>" % ("double" if f64 else "float"))
+        rf["achieved"] = flops / (res["swept"] * 1e-3) / 1e12
+        rf["frac"] = rf["achieved"] / rf["peak"]
+        smem_acc = float((spec["n"] * spec["steps"] * np.where(heat, WORK["heat"]["smem_acc"],
+                                                                2 * smem_ks[f64])).sum())
+        sg = smem_acc * (8 if f64 else 4) / (res["swept"] * 1e-3) / 1e9
+        rf["smem"].update({"achieved": sg, "frac": sg / SMEM_PEAK_GBS})
+        rf["algorithmic_per_unit"] = {"flops": flops / units, "note": "heat and KS point-substeps of the batch"}
+        out[name] = {"ms": res["swept"], "value": ws * work / (res["swept"] * 1e-3), "unit": UNIT,
+                     "classic_ms": res["classic"], "classic_value": ws * work / (res["classic"] * 1e-3),
+                     "speedup_vs_classic": res["classic"] / res["swept"], "tile_w": plan["tile_w"],
+                     "tile_rule": plan.get("rule"),
+                     "threads": plan["threads"], "items": b.items, "timed_runs": runs, "roofline": rf}
         b.close()
         del u, u0
         torch.cuda.empty_cache()
@@ -310,12 +406,16 @@ def measure_sizes(S, autotune, torch, stream, barrier, ws, flush):
                 best = t if best is None else min(best, t)
             res[name] = best
         sol.sync_status()
+        kname, kunits, kms, share = dominant_swept_kernel(sol, u, d0, nsteps, res["swept"])
         sol.close()
+        rf = alu_roofline(scheme, dt == "f64", kunits, kms, kname, registers=bool(plan.get("warp_tiles")))
+        rf["kernel_share"] = share
         out.append({"workload": label, "swept_ms": res["swept"], "classic_ms": res["classic"],
                     "speedup_vs_classic": res["classic"] / res["swept"],
                     "swept_value": ws * n * nsteps / (res["swept"] * 1e-3),
                     "classic_value": ws * n * nsteps / (res["classic"] * 1e-3),
-                    "plan": {k: plan.get(k, 0) for k in ("tile_w", "threads", "warp_tiles", "persistent", "cluster")}})
+                    "plan": {k: plan.get(k, 0) for k in ("tile_w", "threads", "warp_tiles", "persistent", "cluster")},
+                    "roofline": rf})
     return out
 
 
@@ -356,11 +456,16 @@ def measure_heat2d(S, autotune, torch, stream, barrier, ws, flush):
             res[name] = best
         sol.sync_status()
         sol.close()
+        pers = plan.get("persistent", 0)
+        kname = ("k_persist2d<%s>" if pers else "k_pyr2d + k_bridge2d + k_octa2d <%s> (the solve's graph)") % (
+            "double" if dt == "f64" else "float")
+        rf = alu_roofline("heat2d", dt == "f64", n * n * nsteps, res["swept"], kname,
+                          note=None if pers else "per-pass plan: the solve's time, launch gaps included")
         out.append({"workload": label, "swept_ms": res["swept"], "classic_ms": res["classic"],
                     "speedup_vs_classic": res["classic"] / res["swept"],
                     "swept_value": ws * n * n * nsteps / (res["swept"] * 1e-3), "unit": UNIT,
                     "plan": {"tile_w": plan["tile_w"], "threads": plan["threads"],
-                             "persistent": plan.get("persistent", 0)}})
+                             "persistent": plan.get("persistent", 0)}, "roofline": rf})
     return out
 
 
@@ -413,7 +518,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-sizes", action="store_true")
     ap.add_argument("--no-2d", action="store_true")
-    ap.add_argument("--batch-f64", action="store_true", help="also time the FP64 batch (about 50 s)")
+    ap.add_argument("--no-batch-f64", action="store_true", help="skip the FP64 batch (about 2 x 50 s)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -547,7 +652,7 @@ def main():
         heat2d = measure_heat2d(S, autotune, torch, stream, barrier, ws, flush)
     batched = None
     if not args.no_batch:
-        batched = measure_batch(S, inputs, autotune, torch, stream, barrier, ws, args.batch_f64)
+        batched = measure_batch(S, inputs, autotune, torch, stream, barrier, ws, not args.no_batch_f64)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -7,7 +7,7 @@ GPU at hand, by timing short probes of the real kernels with CUDA events,
 and caches the winners in a JSON file keyed by device, scheme, dtype and size.
 
   tune_single(scheme, dtype, n, ...)  -> {"tile_w", "threads", "warp_tiles", "persistent", "cluster", "ms"}
-  tune_batch(problems, dtype, ...)    -> {"tile_w", "threads", "ms"} for one batch plan
+  tune_batch(problems, dtype, ...)    -> {"tile_w", "threads", "rule", "ms"} for one batch plan
 
 Both only launch the library's kernels through the C ABI.
 """
@@ -194,17 +194,37 @@ def tune_2d(dtype, nx, ny, probe_steps=200, tiles=(16, 32, 64, 128), threads=(25
     return best
 
 
-def tune_batch(problems, dtype, tiles=(128, 256, 512), threads=(64, 128, 256), probe_fraction=0.05,
-               cache=DEFAULT_CACHE, refresh=False, reps=1):
-    """Best (tile_w, threads) for a batch: every candidate is timed on the whole
-    batch with each problem's step count scaled by probe_fraction (at least one
-    pass).  Candidates a problem cannot use (W not dividing n) fall back to the
-    library's default for that problem."""
+def _batch_tile(n, plan):
+    """Tile width of an n-point batch problem under a batch plan: a uniform W
+    where it divides n with two tiles, else the library default (0); or, for a
+    size rule (cap, div), the largest power of two <= min(cap, n // div) that
+    divides n."""
+    rule = plan.get("rule")
+    if rule:
+        cap, div = rule
+        w = 1
+        while w * 2 <= min(cap, n // div):
+            w *= 2
+        while w >= 8 and n % w:
+            w //= 2
+        return w if w >= 8 and n // w >= 2 else 0
+    W = plan["tile_w"]
+    return W if (n % W == 0 and n // W >= 2) else 0
+
+
+def tune_batch(problems, dtype, tiles=(128, 256, 512, 1024), threads=(64, 128, 256),
+               rules=((1024, 4), (1024, 8), (512, 4), (1024, 16)), probe_fraction=0.05, cache=DEFAULT_CACHE,
+               refresh=False, reps=1):
+    """Best plan for a batch: every candidate is timed on the whole batch with
+    each problem's step count scaled by probe_fraction (at least one step).
+    First one tile width for every problem ({"tile_w", "threads"}); then, with
+    the best thread count, tile widths by size class ({"rule": (cap, div)}: the
+    largest power of two up to min(cap, n / div) for each problem)."""
     import torch
 
     sig = (len(problems), int(sum(q["n"] for q in problems)), int(sum(q["nsteps"] for q in problems)))
     table = _load(cache) if cache else {}
-    key = "batch/%s/%d/%d/%d/%d" % ((_device_key(), dtype) + sig)
+    key = "batch2/%s/%d/%d/%d/%d" % ((_device_key(), dtype) + sig)
     if not refresh and key in table:
         return table[key]
     probe = []
@@ -212,23 +232,30 @@ def tune_batch(problems, dtype, tiles=(128, 256, 512), threads=(64, 128, 256), p
         r = dict(q)
         r["nsteps"] = max(1, int(q["nsteps"] * probe_fraction))
         probe.append(r)
+
+    def trial(plan):
+        tried = [dict(q, tile_w=_batch_tile(q["n"], plan)) for q in probe]
+        b = S.Batch(tried, dtype, threads=plan["threads"])
+        u0 = b.pack([q["u0"] for q in problems])
+        u = u0.clone()
+        ms = _time(lambda: (u.copy_(u0), b.run(u)), reps)
+        b.close()
+        del u, u0
+        torch.cuda.empty_cache()
+        return ms
+
     best = None
     for W in tiles:
         for t in threads:
-            trial = []
-            for q in probe:
-                r = dict(q)
-                r["tile_w"] = W if (q["n"] % W == 0 and q["n"] // W >= 2) else 0
-                trial.append(r)
-            b = S.Batch(trial, dtype, threads=t)
-            u0 = b.pack([q["u0"] for q in problems])
-            u = u0.clone()
-            ms = _time(lambda: (u.copy_(u0), b.run(u)), reps)
-            b.close()
-            del u, u0
-            torch.cuda.empty_cache()
+            plan = {"tile_w": W, "threads": t, "rule": None}
+            ms = trial(plan)
             if best is None or ms < best["ms"]:
-                best = {"tile_w": W, "threads": t, "ms": ms, "probe_fraction": probe_fraction}
+                best = dict(plan, ms=ms, probe_fraction=probe_fraction)
+    for rule in rules:
+        plan = {"tile_w": 0, "threads": best["threads"], "rule": list(rule)}
+        ms = trial(plan)
+        if ms < best["ms"]:
+            best = dict(plan, ms=ms, probe_fraction=probe_fraction)
     if cache:
         table = _load(cache)
         table[key] = best
@@ -237,11 +264,6 @@ def tune_batch(problems, dtype, tiles=(128, 256, 512), threads=(64, 128, 256), p
 
 
 def apply_batch_plan(problems, plan):
-    """Problems with the tuned tile width set where it divides n (else library default)."""
-    out = []
-    for q in problems:
-        r = dict(q)
-        W = plan["tile_w"]
-        r["tile_w"] = W if (q["n"] % W == 0 and q["n"] // W >= 2) else 0
-        out.append(r)
-    return out
+    """Problems with the tuned tile width set (a uniform width where it divides n,
+    else the library default; or the plan's size rule)."""
+    return [dict(q, tile_w=_batch_tile(q["n"], plan)) for q in problems]
