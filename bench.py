@@ -46,9 +46,9 @@ FP64_KS_MIX_CEILING = 0.535e12
 # N = 2^20, tile 1024, from an ncu capture; None: no capture of the current kernel
 DIAMOND_TRAFFIC_BYTES = None
 # the same for one k_swept_persist<double, KsOp> launch (a whole 50,000-step solve) of the plan
-# (tile, threads) below: 11.88 MB read + 36.98 MB written in a one-pass ncu capture of just those
-# two counters; reported only when the tuned plan is that plan
-PERSIST_TRAFFIC_BYTES = 48860000
+# (tile, threads) below: 11.56 MB read + 36.78 MB written in an ncu capture of just those two
+# counters and the duration, on the current kernel; reported only when the tuned plan is that plan
+PERSIST_TRAFFIC_BYTES = 48339456
 PERSIST_TRAFFIC_PLAN = (1024, 512)  # (tile, threads) of that capture
 
 
