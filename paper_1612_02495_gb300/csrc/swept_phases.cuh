@@ -20,6 +20,19 @@
 
 namespace swept {
 
+// f(s) for the tiers s = 1..n in order, two per trip: with a stage count that
+// is a compile-time constant (two-stage schemes alternate stages), each call's
+// stage is then a constant the compiler can fold.
+template <class F>
+SW_HD void for_tiers(int n, F&& f) {
+  int s = 1;
+  for (; s + 1 <= n; s += 2) {
+    f(s);
+    f(s + 1);
+  }
+  if (s <= n) f(s);
+}
+
 // Up-triangle (pass 0, Fig. SweptPseudo) or, with hh < h, the trapezoid that
 // starts the remainder: load tile b from u, compute tiers 1..hh, export the
 // 2R edge values of tiers 0..hh-1 on both sides; with write_top, also write
@@ -37,7 +50,7 @@ SW_HD void run_up(Cx& cx, const Geom& g_in, int64_t b, int hh, bool write_top) {
     cx.load_u(0, c, g.R + k, x0 + k);
   });
   cx.sync();
-  for (int s = 1; s <= hh; ++s) cx.level(s, 0, g.R + g.R * s, g.R + w - g.R * s, origin, NO_WALL);
+  for_tiers(hh, [&](int s) { cx.level(s, 0, g.R + g.R * s, g.R + w - g.R * s, origin, NO_WALL); });
   const int per_level = g.C * 2 * g.R;
   const int per_side = hh * per_level;
   cx.for_range(0, 2 * per_side, [&](int i) {
@@ -109,10 +122,10 @@ SW_HD void run_diamond(Cx& cx, const Geom& g_in, int64_t b, int odd, int mode, i
   }
   cx.sync();
   const int wall = window_wall(g, origin, w + 2 * g.R);
-  for (int s = 1; s <= hh; ++s) cx.level(s, 0, dofs + grow_lo(g, s), dofs + grow_hi(g, s), origin, wall);
+  for_tiers(hh, [&](int s) { cx.level(s, 0, dofs + grow_lo(g, s), dofs + grow_hi(g, s), origin, wall); });
   if (mode == MODE_DIAMOND) {
     const int top = wide ? g.h : g.h - 1;  // a triangle's tier h is empty; a wide tile's is its flat top
-    for (int s = 1; s <= top; ++s) cx.level(s, g.h, g.R + g.R * s, g.R + w - g.R * s, origin, wall);
+    for_tiers(top, [&](int s) { cx.level(s, g.h, g.R + g.R * s, g.R + w - g.R * s, origin, wall); });
     const int per_side_h = g.h * per_level;
     cx.for_range(0, 2 * per_side_h, [&](int i) {
       const int side = i >= per_side_h ? 1 : 0;
