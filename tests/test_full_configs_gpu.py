@@ -12,7 +12,7 @@ times (the autotuner's plan from the same call).
     equals the oracle's reverse mode (same segment length) bit for bit, dL/dnu
     is within the derived bound, and 8 seeded directions plus dL/dnu agree
     with central differences of GPU forward solves;
-  - the batched workload (4096 problems) in FP64, sampled.
+  - the batched workload (4096 problems) in FP64 and FP32, sampled.
 
 These take minutes of host time (the oracle is plain C); they are marked slow.
 """
@@ -202,18 +202,23 @@ def test_adjoint_configured_size_central_differences(S):
 
 
 # --------------------------------------------------------------------------- batched FP64
-def test_full_batch_workload_f64_bench_plan(S):
-    """The batched workload in FP64 (4096 problems) with the tuned batch plan
-    bench.py uses: sampled problems equal their standalone swept solves bit for
-    bit, and the four smallest plus two sampled ones equal the oracle."""
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_full_batch_workload_bench_plan(S, dtype):
+    """The batched workload (4096 problems) with the tuned batch plan bench.py
+    uses: sampled problems equal their standalone swept solves bit for bit, and
+    the four smallest plus two sampled ones equal the oracle."""
     import torch
 
     from paper_1612_02495_gb300 import autotune
 
-    probs = inputs.batch_instances(inputs.batch_problems(), dtype=np.float64)
-    plan = autotune.tune_batch(probs, S.F64)
+    code = S.F64 if dtype == np.float64 else S.F32
+    probs = inputs.batch_instances(inputs.batch_problems(), dtype=dtype)
+    if code == S.F64:
+        plan = autotune.tune_batch(probs, code, tiles=(512, 1024), threads=(128, 256), rules=((1024, 8),))
+    else:
+        plan = autotune.tune_batch(probs, code)
     tuned = autotune.apply_batch_plan(probs, plan)
-    b = S.Batch(tuned, S.F64, threads=plan["threads"])
+    b = S.Batch(tuned, code, threads=plan["threads"])
     u = b.pack([q["u0"] for q in probs])
     b.run(u)
     torch.cuda.synchronize()
@@ -226,7 +231,7 @@ def test_full_batch_workload_f64_bench_plan(S):
     sample = [int(i) for i in rng.choice(len(probs), size=12, replace=False)]
     for i in sample:
         q = tuned[i]
-        sol = S.Solver(q["scheme"], S.F64, q["n"], q["dx"], q["dt"], q["param"], tile_w=q["tile_w"])
+        sol = S.Solver(q["scheme"], code, q["n"], q["dx"], q["dt"], q["param"], tile_w=q["tile_w"])
         x = torch.from_numpy(q["u0"]).cuda()
         sol.step(x, q["nsteps"])
         torch.cuda.synchronize()
