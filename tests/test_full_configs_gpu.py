@@ -142,12 +142,11 @@ def test_adjoint_configured_size_matches_oracle_reverse_mode(S):
     g, gnu = sol.adjoint(torch.from_numpy(gT).cuda(), ADJ_STEPS, ck, u0=torch.from_numpy(p["u0"]).cuda())
     torch.cuda.synchronize()
     sol.sync_status()
-    # the library's default segment: whole passes of h/S steps, about sqrt(nsteps * h/S) steps
+    # the library's default segment: the whole number of passes (h/S steps each)
+    # with the fewest stored states, ceil(nsteps / K) checkpoints + an S K + 1 tier tape
     k0 = sol.plan["half_cycle"] // sol.plan["stages"]
-    m = 1
-    while (m + 1) * (m + 1) * k0 <= ADJ_STEPS:
-        m += 1
-    seg = min(ADJ_STEPS, m * k0)
+    S_ = sol.plan["stages"]
+    seg = min(range(k0, ADJ_STEPS + 1, k0), key=lambda K: (-(-ADJ_STEPS // K) + S_ * K + 1, K))
     sol.close()
     ref, ref_nu, cond = oracle.ks_adjoint(p["u0"], p["dx"], p["dt"], 1.0, ADJ_STEPS, gT, seg=seg,
                                           with_condition=True, threads=HOST_THREADS)
