@@ -87,10 +87,9 @@ typedef enum {
  *            and warp_tiles modes need W to divide n.
  *   threads  threads per block, 0 = chosen by the library (<= 1024, multiple of 32)
  *   chunk    heat and KS: 1 = one point per thread per trip through a tier
- *            (strided, the default); 2 = two strided points (j, j + threads)
- *            with both windows loaded first; 3..9 (odd) = that many consecutive
- *            points from one register window (odd so shared-memory accesses
- *            are conflict-free).  Euler: 1 = one thread per face in the flux
+ *            (strided; in FP32, radius-2 tiers take aligned pairs of points,
+ *            the default); 2 = two strided points (j, j + threads) with both
+ *            windows loaded first.  Euler: 1 = one thread per face in the flux
  *            phase of a tier; 2 = two threads per face (one per reconstructed
  *            side, exchanged by warp shuffle)
  *   persistent 0: one kernel launch per swept pass (graph-captured); 1: the
@@ -121,7 +120,7 @@ typedef struct {
   double param[4];
   int32_t tile_w;
   int32_t threads;
-  int32_t chunk;    /* heat/KS points per thread per trip: 1, 2 (strided pairs), 3, 5, 7, 9; Euler: threads per face, 1 or 2; 0 = 1 */
+  int32_t chunk;    /* heat/KS: 1, or 2 (two strided points a trip); Euler: threads per face, 1 or 2; 0 = 1 */
   int32_t persistent; /* 1: swept_step_n runs all passes in one persistent kernel */
   int32_t cluster;    /* 1: the whole grid (2..16 tiles) is one thread-block cluster */
   int32_t warp_tiles; /* 1: one warp per tile, tier rows in registers, neighbours by warp shuffle */

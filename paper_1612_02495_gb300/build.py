@@ -23,7 +23,8 @@ LIB = os.path.join(HERE, "libswept.so")
 BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 LIB_DEBUG = os.path.join(HERE, "libswept_debug.so")
 
-SOURCES = ["api.cu", "impl_heat.cu", "impl_ks.cu", "impl_euler.cu", "check.cpp", "noalloc.cu", "batch.cu", "api2d.cu",
+SOURCES = ["api.cu", "impl_heat_f32.cu", "impl_heat_f64.cu", "impl_ks_f32.cu", "impl_ks_f64.cu", "impl_euler_f32.cu",
+           "impl_euler_f64.cu", "check.cpp", "noalloc.cu", "batch.cu", "api2d.cu",
            "check2d.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "--fmad=false", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",

@@ -359,8 +359,7 @@ swept_status swept_init(const swept_config* cfg, swept_handle** out) {
   // mapping measured slower at every size (the tiers are latency-bound, and
   // spreading a tier over more warps beats fewer shared-memory reads)
   g.chunk = cfg->chunk > 0 ? cfg->chunk : 1;
-  if ((g.chunk != 1 && g.chunk != 2 && g.chunk != 3 && g.chunk != 5 && g.chunk != 7 && g.chunk != 9) ||
-      (im->C == 3 && g.chunk > 2)) {  // Euler: 1 or 2 (two threads per face)
+  if (g.chunk != 1 && g.chunk != 2) {  // heat/KS: strided pairs; Euler: two threads per face
     delete h;
     return SWEPT_EINVAL;
   }

@@ -1,5 +1,5 @@
 // Per-(scheme, dtype) launch table, filled by one translation unit per scheme
-// (impl_heat.cu, impl_ks.cu, impl_euler.cu) and used by the runtime (api.cu).
+// (impl_<scheme>_f32.cu / impl_<scheme>_f64.cu) and used by the runtime (api.cu).
 #pragma once
 #include <cuda_runtime.h>
 #include <stddef.h>
@@ -65,5 +65,11 @@ cudaError_t raise_smem_limit(const void* fn, size_t bytes);
 const SchemeImpl* heat_impl(int dtype);
 const SchemeImpl* ks_impl(int dtype);
 const SchemeImpl* euler_impl(int dtype);
+const SchemeImpl* heat_impl_f32();
+const SchemeImpl* heat_impl_f64();
+const SchemeImpl* ks_impl_f32();
+const SchemeImpl* ks_impl_f64();
+const SchemeImpl* euler_impl_f32();
+const SchemeImpl* euler_impl_f64();
 
 }  // namespace swept

@@ -1,4 +1,8 @@
-// 1D Euler (MUSCL-minmod + Rusanov + SSP-RK2) instantiation of the kernels.
+// 1D Euler (MUSCL-minmod + Rusanov + SSP-RK2):
+// the scheme's constants and launch-table builders, shared by the FP32 and
+// FP64 translation units (impl_euler_f32.cu, impl_euler_f64.cu), which compile in
+// parallel.
+#pragma once
 #include "impl_common.cuh"
 
 namespace swept {
@@ -39,11 +43,5 @@ SchemeImpl make_euler() {
   return im;
 }
 
-const SchemeImpl kEulerF32 = make_euler<float>();
-const SchemeImpl kEulerF64 = make_euler<double>();
-
 }  // namespace
-
-const SchemeImpl* euler_impl(int dtype) { return dtype == 0 ? &kEulerF32 : &kEulerF64; }
-
 }  // namespace swept

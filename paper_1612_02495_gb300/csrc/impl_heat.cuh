@@ -1,4 +1,8 @@
-// Heat (FTCS, Eq. HeatDisc) instantiation of the swept and classic kernels.
+// Heat (FTCS, Eq. HeatDisc):
+// the scheme's constants and launch-table builders, shared by the FP32 and
+// FP64 translation units (impl_heat_f32.cu, impl_heat_f64.cu), which compile in
+// parallel.
+#pragma once
 #include "impl_common.cuh"
 
 namespace swept {
@@ -43,11 +47,5 @@ SchemeImpl make_heat_f64() {
   return im;
 }
 
-const SchemeImpl kHeatF32 = make_heat<float>();
-const SchemeImpl kHeatF64 = make_heat_f64();
-
 }  // namespace
-
-const SchemeImpl* heat_impl(int dtype) { return dtype == 0 ? &kHeatF32 : &kHeatF64; }
-
 }  // namespace swept

@@ -1,4 +1,8 @@
-// Kuramoto-Sivashinsky (Eq. KSDisc + midpoint RK2) instantiation of the kernels.
+// Kuramoto-Sivashinsky (Eq. KSDisc + midpoint RK2):
+// the scheme's constants and launch-table builders, shared by the FP32 and
+// FP64 translation units (impl_ks_f32.cu, impl_ks_f64.cu), which compile in
+// parallel.
+#pragma once
 #include "impl_common.cuh"
 
 namespace swept {
@@ -51,11 +55,5 @@ SchemeImpl make_ks_f64() {
   return im;
 }
 
-const SchemeImpl kKsF32 = make_ks<float>();
-const SchemeImpl kKsF64 = make_ks_f64();
-
 }  // namespace
-
-const SchemeImpl* ks_impl(int dtype) { return dtype == 0 ? &kKsF32 : &kKsF64; }
-
 }  // namespace swept

@@ -50,37 +50,6 @@ __device__ __forceinline__ void scalar_level(T* sm, int M, int out_row, int lo, 
   }
 }
 
-// Same tier with each thread advancing `P` consecutive points from a register
-// window of P + 2R values: shared-memory reads per point drop from 2R + 1 to
-// (P + 2R) / P, and P odd keeps the stride-P accesses free of bank conflicts.
-// Inputs past hi + R - 1 (the last one an output in [lo, hi) needs) are
-// clamped, not read; the outputs they would feed are discarded.
-template <typename T, class Op, int STAGE, int P>
-__device__ __forceinline__ void chunked_level(T* sm, int M, int out_row, int lo, int hi, const typename Op::K& k) {
-  constexpr int R = Op::R;
-  const T* in = sm + (out_row ^ 1) * M;
-  T* out = sm + out_row * M;
-  const int lim = hi + R - 1;
-  const int nch = (hi - lo + P - 1) / P;
-  for (int c = (int)threadIdx.x; c < nch; c += (int)blockDim.x) {
-    const int j0 = lo + c * P;
-    // all loads first, then all P updates in registers, then all stores, so the
-    // stores to the output row cannot order the next point's loads behind them
-    T win[P + 2 * R];
-    T p2[P];
-    T res[P];
-#pragma unroll
-    for (int q = 0; q < P + 2 * R; ++q) win[q] = in[min(j0 - R + q, lim)];
-#pragma unroll
-    for (int q = 0; q < P; ++q) p2[q] = STAGE == 1 ? out[min(j0 + q, hi - 1)] : T(0);
-#pragma unroll
-    for (int q = 0; q < P; ++q) res[q] = Op::template point<STAGE>(&win[q], p2[q], k);
-#pragma unroll
-    for (int q = 0; q < P; ++q)
-      if (j0 + q < hi) out[j0 + q] = res[q];
-  }
-}
-
 // Strided mapping with two points per thread per trip (j and j + blockDim.x):
 // both windows are loaded before either result is stored, so each thread has
 // two independent update chains in flight.
@@ -158,16 +127,7 @@ __device__ __forceinline__ void scalar_level_any(T* sm, int M, int out_row, int 
     scalar_level<T, Op, STAGE>(sm, M, out_row, lo, hi, wall, k);
     return;
   }
-  if (chunk == 2) {
-    strided2_level<T, Op, STAGE>(sm, M, out_row, lo, hi, k);
-    return;
-  }
-  switch (chunk) {
-    case 3: chunked_level<T, Op, STAGE, 3>(sm, M, out_row, lo, hi, k); break;
-    case 5: chunked_level<T, Op, STAGE, 5>(sm, M, out_row, lo, hi, k); break;
-    case 7: chunked_level<T, Op, STAGE, 7>(sm, M, out_row, lo, hi, k); break;
-    default: chunked_level<T, Op, STAGE, 9>(sm, M, out_row, lo, hi, k); break;
-  }
+  strided2_level<T, Op, STAGE>(sm, M, out_row, lo, hi, k);
 }
 
 // ---------------------------------------------------------------------------
@@ -412,7 +372,7 @@ struct DevCtx {
   __device__ __forceinline__ void level(int s, int base, int lo, int hi, int64_t origin, int wall) {
     if (dbg::level(g.M, lo, hi, kR)) LevelImpl<T, Op>::run(sm, g.M, stage_c<Op>(s), s & 1, lo, hi, wall, g.chunk, k);
     if (TAPE) {
-      // the tier's mapping of points to threads (strided, paired or chunked)
+      // the tier's mapping of points to threads (strided or paired)
       // need not match this loop's, so the tier must be complete first
       __syncthreads();
       const int64_t slot = tape.base + base + s - tape.tier0;
@@ -561,8 +521,8 @@ __device__ __forceinline__ typename WithTiers<Base, P>::type tiers_ctx(const Bas
 
 // Launch bounds of the swept kernels.  P > 0: one warp per block, 16 blocks
 // per SM.  Shared-memory tiers: MAXT threads at most; MAXT = 1024 caps a
-// thread at 64 registers; MAXT = 256 (the variant Euler runs with up to 256
-// threads) at 85 with 3 blocks per SM, which measured faster on the Euler
+// thread at 64 registers; MAXT = 256 (the variant blocks of up to 256 threads
+// run) at 85 with 3 blocks per SM, which measured faster on the Euler
 // workloads than 2 blocks of up to 128 registers.
 #define SWEPT_BOUNDS(P, MAXT) __launch_bounds__((P) > 0 ? 32 : (MAXT), (P) > 0 ? 16 : ((MAXT) <= 256 ? 3 : 1))
 

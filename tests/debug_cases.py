@@ -71,7 +71,7 @@ def main():
         for n, W, nsteps, extra in [(3 * 128, 128, 257, {}), (2048, 64, 203, {"persistent": 1}),
                                     (8 * 128, 128, 99, {"cluster": 1}), (2048, 64, 101, {"warp_tiles": 1}),
                                     (4096, 256, 150, {"warp_tiles": 1, "persistent": 1}),
-                                    (2048, 128, 77, {"chunk": 3}), (2048, 128, 77, {"chunk": 2})]:
+                                    (2048, 128, 77, {"chunk": 2})]:
             p = inputs.ks_problem(n=n, dtype=dtype)
             ref = oracle.ks(p["u0"], p["dx"], p["dt"], p["nu"], nsteps, threads=8)
             run1d(S.KS, code, p["u0"], (p["dx"], p["dt"], p["nu"]), nsteps, ref, tile_w=W, **extra)

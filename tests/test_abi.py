@@ -58,6 +58,7 @@ def cfg(S, scheme=None, **kw):
     dict(warp_tiles=1, tile_w=64, threads=64), dict(warp_tiles=1, tile_w=64, chunk=3),
     dict(warp_tiles=1, scheme=2, tile_w=64, param0=1.4, bc=1),  # Euler keeps its tiers in shared memory
     dict(chunk=3, scheme=2, tile_w=64, param0=1.4, bc=1),  # Euler: one or two threads per face
+    dict(chunk=3), dict(chunk=5),  # heat/KS: one or two points a trip
 ])
 def test_init_rejects_invalid_configs(S, bad):
     if bad.get("scheme") == 2:

@@ -184,14 +184,13 @@ def test_ks_full_size_sampled(S):
     sol.close()
 
 
-@pytest.mark.parametrize("chunk", [1, 3, 5, 7, 9])
+@pytest.mark.parametrize("chunk", [1, 2])
 @pytest.mark.parametrize("scheme,dtype", [("ks", np.float64), ("ks", np.float32), ("heat", np.float64),
                                           ("heat", np.float32)])
 def test_chunked_tiers_parity(S, chunk, scheme, dtype):
-    """Each thread advancing `chunk` consecutive points from a register window
-    gives the same bits as the strided mapping and the oracle (ragged tiers:
-    widths not multiples of the chunk, tile 96/192, thread counts below the
-    chunk count)."""
+    """One point a thread per trip (paired in FP32 KS) and two strided points a
+    trip give the same bits as the oracle (tile 96/192, 32 threads: tiers wider
+    than the block, ragged trip counts)."""
     code = S.F64 if dtype == np.float64 else S.F32
     if scheme == "ks":
         p = inputs.ks_problem(n=192 * 8, dtype=dtype)
