@@ -25,7 +25,7 @@ LIB_DEBUG = os.path.join(HERE, "libswept_debug.so")
 
 SOURCES = ["api.cu", "impl_heat_f32.cu", "impl_heat_f64.cu", "impl_ks_f32.cu", "impl_ks_f64.cu", "impl_euler_f32.cu",
            "impl_euler_f64.cu", "check.cpp", "noalloc.cu", "batch.cu", "api2d.cu",
-           "check2d.cpp"]
+           "check2d.cpp", "slab.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "--fmad=false", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
           "-I", INCLUDE, "-I", CSRC]
@@ -39,7 +39,7 @@ def _nvcc():
 
 
 def _deps():
-    return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "swept.h"), os.path.join(INCLUDE, "swept2d.h"), __file__]
+    return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)] + [__file__]
 
 
 def _stale(lib):

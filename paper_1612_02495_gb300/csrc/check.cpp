@@ -10,6 +10,10 @@
 //   - blocks of one launch never touch a global location another block of the
 //     same launch writes (no race between blocks);
 //   - at the end the state holds tier n_sub at every point.
+// For a slab of a grid split over ranks (swept_slab_check and the per-rank
+// swept_slab_sym_* replay) each rank's blocks run over that rank's own state
+// array and edge buffers, and the transfers of slab_xfers move tags between
+// the ranks' buffers; the same invariants are checked over all ranks.
 // For a persistent handle the replay runs the persistent kernel's item queue
 // instead of launches.  Its blocks order themselves only through the waits of
 // persist_deps, so the check there is on the happens-before relation those
@@ -18,11 +22,14 @@
 // every item that read that earlier value.
 #include <stdio.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
 #include "runtime.h"
+#include "slab_plan.h"
 #include "swept_phases.cuh"
+#include "swept_slab.h"
 
 namespace swept {
 namespace {
@@ -358,3 +365,250 @@ swept_status check_schedule(swept_handle* h, int64_t nsteps, int64_t* computed) 
 }
 
 }  // namespace swept
+
+// ---------------------------------------------------------------------------
+// slab replay: one rank of a grid split over ranks (slab_plan.h)
+// ---------------------------------------------------------------------------
+namespace swept {
+namespace {
+
+// HostCtx over a slab: the state at c ul + (x - x0), edge slots by slab_slot
+struct SlabHostCtx : HostCtx {
+  static constexpr bool kSlab = true;
+  Slab sl;
+  SlabHostCtx(Sim& s, const Slab& slab, int64_t b, int64_t base, int ei, int eo)
+      : HostCtx(s, b, base, ei, eo), sl(slab) {}
+  bool state_index(int c, int64_t x, size_t* out) {
+    const int64_t i = x - sl.x0;
+    if (i < 0 || i >= sl.ul) {
+      char b[160];
+      snprintf(b, sizeof b, "block %lld touches point %lld outside the slab's state array [%lld, %lld)",
+               (long long)block, (long long)x, (long long)sl.x0, (long long)(sl.x0 + sl.ul));
+      sim.fail(b);
+      return false;
+    }
+    *out = (size_t)(c * sl.ul + i);
+    return true;
+  }
+  void load_u(int r, int c, int j, int64_t x) {
+    size_t i;
+    if (!state_index(c, x, &i)) return;
+    sim.note(BUF_U, i, block, false, "u");
+    cell(r, c, j) = sim.u[i];
+  }
+  void store_u(int r, int c, int j, int64_t x) {
+    size_t i;
+    if (!state_index(c, x, &i)) return;
+    sim.note(BUF_U, i, block, true, "u");
+    const Tag t = cell(r, c, j);
+    if (t.x != wrap_n(x, g.N)) sim.fail("store_u writes a value of another point");
+    sim.u[i] = t;
+  }
+};
+
+}  // namespace
+
+// the plan and slab of swept_slab_init (slab.cu)
+swept_status slab_plan(const swept_config* cfg, int rank, int nranks, Geom* g, Slab* sl, swept_handle** plan_out);
+
+}  // namespace swept
+
+struct swept_slab_sym {
+  swept::Geom g;
+  swept::Slab sl;
+  int64_t n_sub = 0;
+  swept::Sim sim;
+};
+
+namespace {
+
+void set_msg(char* msg, size_t len, const std::string& m) {
+  if (msg && len > 0) snprintf(msg, len, "%s", m.c_str());
+}
+
+swept_status sym_fail(swept_slab_sym* s, char* msg, size_t len) {
+  set_msg(msg, len, s->sim.err);
+  return SWEPT_EDEVICE;
+}
+
+}  // namespace
+
+extern "C" {
+
+swept_status swept_slab_sym_init(const swept_config* cfg, int32_t rank, int32_t nranks, int64_t nsteps,
+                                 swept_slab_sym** out) {
+  using namespace swept;
+  if (!out || nsteps < 0) return SWEPT_EINVAL;
+  *out = nullptr;
+  Geom g;
+  Slab sl;
+  const swept_status st = slab_plan(cfg, rank, nranks, &g, &sl, nullptr);
+  if (st != SWEPT_OK) return st;
+  const int64_t n_sub = nsteps * g.S;
+  if ((double)(n_sub + 1) * (double)g.N > 4e8) return SWEPT_EINVAL;
+  swept_slab_sym* s = new swept_slab_sym();
+  s->g = g;
+  s->sl = sl;
+  s->n_sub = n_sub;
+  Sim& sim = s->sim;
+  sim.g = g;
+  sim.n_sub = n_sub;
+  const int64_t x1 = slab_end(g, sl);
+  sim.u.assign((size_t)(g.C * sl.ul), Tag{});
+  for (int c = 0; c < g.C; ++c)
+    for (int64_t x = sl.x0; x < x1; ++x) sim.u[(size_t)(c * sl.ul + (x - sl.x0))] = Tag{x, 0};
+  sim.au.assign(sim.u.size(), Access{});
+  for (int b = 0; b < 2; ++b) {
+    sim.e[b].assign((size_t)slab_edge_values(g, sl), Tag{});
+    sim.ae[b].assign(sim.e[b].size(), Access{});
+  }
+  sim.count.assign((size_t)(n_sub + 1) * g.N, 0);
+  *out = s;
+  return SWEPT_OK;
+}
+
+swept_status swept_slab_sym_buffer(swept_slab_sym* s, int32_t region, int64_t** tags, int64_t* values) {
+  if (!s || !tags || !values || region < 0 || region > 2) return SWEPT_EINVAL;
+  std::vector<swept::Tag>& v = region == 2 ? s->sim.u : s->sim.e[region];
+  static_assert(sizeof(swept::Tag) == 2 * sizeof(int64_t), "a tag is two int64 (point, sub-timestep)");
+  *tags = reinterpret_cast<int64_t*>(v.data());
+  *values = (int64_t)v.size();
+  return SWEPT_OK;
+}
+
+swept_status swept_slab_sym_launch(swept_slab_sym* s, int64_t i, char* msg, size_t len) {
+  using namespace swept;
+  if (!s) return SWEPT_EINVAL;
+  const Geom& g = s->g;
+  if (i < 0 || i >= launch_total(g, s->n_sub)) return SWEPT_EINVAL;
+  Sim& sim = s->sim;
+  ++sim.stamp;
+  const LaunchDesc d = launch_at(g, s->n_sub, i);
+  const int64_t q = s->n_sub / g.h;
+  const int64_t base = d.pass >= 0 ? (d.kind == 0 ? 0 : (d.pass - 1) * (int64_t)g.h) : q * (int64_t)g.h;
+  for (int64_t b = s->sl.b0; b < s->sl.b0 + s->sl.nb && sim.err.empty(); ++b) {
+    SlabHostCtx cx(sim, s->sl, b, base, d.ein, d.eout);
+    if (d.kind == 0)
+      run_up(cx, g, b, d.hh, d.mode == MODE_GAP);
+    else
+      run_diamond(cx, g, b, d.odd, d.mode, d.hh);
+  }
+  if (!sim.err.empty()) return sym_fail(s, msg, len);
+  return SWEPT_OK;
+}
+
+swept_status swept_slab_sym_finish(swept_slab_sym* s, int32_t* counts, char* msg, size_t len) {
+  using namespace swept;
+  if (!s || !counts) return SWEPT_EINVAL;
+  Sim& sim = s->sim;
+  const Geom& g = s->g;
+  const int64_t x1 = slab_end(g, s->sl);
+  for (int c = 0; c < g.C && sim.err.empty(); ++c)
+    for (int64_t x = s->sl.x0; x < x1; ++x) {
+      const Tag t = sim.u[(size_t)(c * s->sl.ul + (x - s->sl.x0))];
+      if (t.x != x || t.lvl != s->n_sub) {
+        char b[200];
+        snprintf(b, sizeof b, "final state at point %lld holds (point %lld, tier %lld), expected tier %lld",
+                 (long long)x, (long long)t.x, (long long)t.lvl, (long long)s->n_sub);
+        sim.fail(b);
+        break;
+      }
+    }
+  if (!sim.err.empty()) return sym_fail(s, msg, len);
+  for (size_t i = 0; i < sim.count.size(); ++i) counts[i] += sim.count[i];
+  return SWEPT_OK;
+}
+
+void swept_slab_sym_free(swept_slab_sym* s) { delete s; }
+
+swept_status swept_slab_check(const swept_config* cfg, int32_t nranks, int64_t nsteps, int64_t* computed, char* msg,
+                              size_t len) {
+  using namespace swept;
+  if (!cfg || nranks < 1 || nsteps < 0) return SWEPT_EINVAL;
+  std::vector<swept_slab_sym*> r((size_t)nranks, nullptr);
+  auto cleanup = [&]() {
+    for (auto* p : r) swept_slab_sym_free(p);
+  };
+  for (int k = 0; k < nranks; ++k) {
+    const swept_status st = swept_slab_sym_init(cfg, k, nranks, nsteps, &r[(size_t)k]);
+    if (st != SWEPT_OK) {
+      cleanup();
+      set_msg(msg, len, "swept_slab_sym_init failed");
+      return st;
+    }
+  }
+  const Geom& g = r[0]->g;
+  const int64_t n_sub = r[0]->n_sub;
+  const int64_t total = launch_total(g, n_sub);
+  std::vector<std::vector<Xfer>> xs((size_t)nranks);
+  for (int64_t i = 0; i < total; ++i) {
+    for (int k = 0; k < nranks; ++k) {
+      const swept_status st = swept_slab_sym_launch(r[(size_t)k], i, msg, len);
+      if (st != SWEPT_OK) {
+        cleanup();
+        return st;
+      }
+    }
+    for (int k = 0; k < nranks; ++k) {
+      Xfer x[8];
+      const int m = slab_xfers(g, r[(size_t)k]->sl, n_sub, i, x);
+      xs[(size_t)k].assign(x, x + m);
+    }
+    // the j-th send of rank k to side p lands in the j-th receive of rank k + p from side -p
+    for (int k = 0; k < nranks; ++k) {
+      for (int p : {-1, +1}) {
+        const int q = ((k + p) % nranks + nranks) % nranks;
+        std::vector<const Xfer*> sends, recvs;
+        for (const Xfer& x : xs[(size_t)k])
+          if (!x.recv && x.peer == p) sends.push_back(&x);
+        for (const Xfer& x : xs[(size_t)q])
+          if (x.recv && x.peer == -p) recvs.push_back(&x);
+        if (sends.size() != recvs.size()) {
+          cleanup();
+          set_msg(msg, len, "sends and receives between neighbours do not pair up");
+          return SWEPT_EDEVICE;
+        }
+        for (size_t j = 0; j < sends.size(); ++j) {
+          const Xfer& a = *sends[j];
+          const Xfer& b = *recvs[j];
+          std::vector<Tag>& src = a.region == 2 ? r[(size_t)k]->sim.u : r[(size_t)k]->sim.e[a.region];
+          std::vector<Tag>& dst = b.region == 2 ? r[(size_t)q]->sim.u : r[(size_t)q]->sim.e[b.region];
+          if (a.count != b.count || a.offset < 0 || b.offset < 0 || a.offset + a.count > (int64_t)src.size() ||
+              b.offset + b.count > (int64_t)dst.size()) {
+            cleanup();
+            set_msg(msg, len, "a transfer's count or range does not fit its buffers");
+            return SWEPT_EDEVICE;
+          }
+          const std::vector<Tag> tmp(src.begin() + a.offset, src.begin() + a.offset + a.count);
+          std::copy(tmp.begin(), tmp.end(), dst.begin() + b.offset);
+        }
+      }
+    }
+  }
+  std::vector<int32_t> counts((size_t)(n_sub + 1) * g.N, 0);
+  int64_t sum = 0;
+  for (int k = 0; k < nranks; ++k) {
+    const swept_status st = swept_slab_sym_finish(r[(size_t)k], counts.data(), msg, len);
+    if (st != SWEPT_OK) {
+      cleanup();
+      return st;
+    }
+    sum += r[(size_t)k]->sim.computed;
+  }
+  for (int64_t L = 1; L <= n_sub; ++L)
+    for (int64_t x = 0; x < g.N; ++x)
+      if (counts[(size_t)(L * g.N + x)] != 1) {
+        char b[160];
+        snprintf(b, sizeof b, "point %lld of tier %lld computed %d times over all ranks", (long long)x, (long long)L,
+                 (int)counts[(size_t)(L * g.N + x)]);
+        set_msg(msg, len, b);
+        cleanup();
+        return SWEPT_EDEVICE;
+      }
+  if (computed) *computed = sum;
+  cleanup();
+  set_msg(msg, len, "");
+  return SWEPT_OK;
+}
+
+}  // extern "C"

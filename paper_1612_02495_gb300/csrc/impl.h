@@ -53,6 +53,13 @@ struct SchemeImpl {
   cudaError_t (*adj_diamond)(const Geom& g, const void* ka, void* lam_out, const void* e_in, void* e_out, int odd,
                              int mode, int hh, int threads, size_t smem, const void* tape, int64_t top, int64_t base,
                              double* slots, cudaStream_t s);
+  // one pass of a slab of a grid split over ranks (blocks [sl.b0, sl.b0 + sl.nb));
+  // slab_prepare raises the slab kernels' shared-memory limit
+  cudaError_t (*slab_prepare)(size_t bytes);
+  cudaError_t (*slab_up)(const Geom& g, const Slab& sl, const void* k, const void* u_in, void* u_out, void* e_out,
+                         int hh, int write_top, int threads, size_t smem, cudaStream_t s);
+  cudaError_t (*slab_diamond)(const Geom& g, const Slab& sl, const void* k, void* u_out, const void* e_in,
+                              void* e_out, int odd, int mode, int hh, int threads, size_t smem, cudaStream_t s);
 };
 
 // Raise kernel `fn`'s dynamic shared-memory limit on the current device to at

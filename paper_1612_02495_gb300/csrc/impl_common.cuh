@@ -147,6 +147,29 @@ struct Launch {
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, fn, g, kc(k), (T*)u, n_sub, win_values);
   }
+  static cudaError_t slab_prepare(size_t bytes) {
+    cudaError_t e = raise_smem_limit((const void*)k_slab_up<T, Op>, bytes);
+    if (e == cudaSuccess) e = raise_smem_limit((const void*)k_slab_diamond<T, Op>, bytes);
+    return e;
+  }
+  static cudaError_t slab_up(const Geom& g, const Slab& sl, const void* k, const void* u_in, void* u_out, void* e_out,
+                             int hh, int write_top, int threads, size_t smem, cudaStream_t s) {
+    return with_p(g.P, [&](auto pc) {
+      constexpr int P = decltype(pc)::value;
+      k_slab_up<T, Op, P><<<(unsigned)sl.nb, threads, smem, s>>>(g, sl, kc(k), (const T*)u_in, (T*)u_out,
+                                                                  (T*)e_out, hh, write_top);
+      return cudaGetLastError();
+    });
+  }
+  static cudaError_t slab_diamond(const Geom& g, const Slab& sl, const void* k, void* u_out, const void* e_in,
+                                  void* e_out, int odd, int mode, int hh, int threads, size_t smem, cudaStream_t s) {
+    return with_p(g.P, [&](auto pc) {
+      constexpr int P = decltype(pc)::value;
+      k_slab_diamond<T, Op, P><<<(unsigned)sl.nb, threads, smem, s>>>(g, sl, kc(k), (T*)u_out, (const T*)e_in,
+                                                                       (T*)e_out, odd, mode, hh);
+      return cudaGetLastError();
+    });
+  }
   static Tape<T> mk_tape(void* tape, int64_t tier0, int64_t ntiers, int64_t base) {
     Tape<T> t;
     t.p = (T*)tape;

@@ -40,6 +40,9 @@ SchemeImpl make_euler() {
   SchemeImpl im{2, 2, 3, (int)sizeof(T), euler_consts<T>, L::smem_values, L::prepare, L::up, L::diamond,
                 euler_classic<T>, L::copy, L::persist, L::persist_blocks_per_sm, L::cluster, L::up_tape, L::diamond_tape, nullptr,
                 nullptr, nullptr, nullptr};
+  im.slab_prepare = L::slab_prepare;
+  im.slab_up = L::slab_up;
+  im.slab_diamond = L::slab_diamond;
   return im;
 }
 

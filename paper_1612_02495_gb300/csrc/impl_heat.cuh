@@ -34,6 +34,9 @@ SchemeImpl make_heat() {
   SchemeImpl im{1, 1, 1, (int)sizeof(T), heat_consts<T>, L::smem_values, L::prepare, L::up, L::diamond,
                 L::classic, L::copy, L::persist, L::persist_blocks_per_sm, L::cluster, L::up_tape, L::diamond_tape, nullptr,
                 nullptr, nullptr, nullptr};
+  im.slab_prepare = L::slab_prepare;
+  im.slab_up = L::slab_up;
+  im.slab_diamond = L::slab_diamond;
   return im;
 }
 

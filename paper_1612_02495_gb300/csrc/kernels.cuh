@@ -748,6 +748,54 @@ __global__ void SWEPT_BOUNDS(P, MAXT) k_swept_diamond(Geom g, typename Op::K k, 
   run_diamond(cx, g, (int64_t)blockIdx.x, odd, mode, hh);
 }
 
+// ---------------------------------------------------------------------------
+// one slab of a grid split over ranks (Slab, swept_geom.cuh): the same pass
+// phases over blocks [b0, b0 + nb), with the state at index c ul + (x - x0)
+// (no wrap-around) and the edge slots of the slab's own buffers
+// ---------------------------------------------------------------------------
+template <typename T, class Op>
+struct SlabCtx : DevCtx<T, Op> {
+  static constexpr bool kSlab = true;
+  Slab sl;
+
+  __device__ __forceinline__ void load_u(int r, int c, int j, int64_t x) {
+    const int64_t i = x - sl.x0;
+    if (dbg::win(this->g.M, r, c, Op::C, j) && dbg::in_range(i, sl.ul, dbg::STATE))
+      this->row(r, c)[j] = this->u_in[c * sl.ul + i];
+  }
+  __device__ __forceinline__ void store_u(int r, int c, int j, int64_t x) {
+    const int64_t i = x - sl.x0;
+    if (dbg::win(this->g.M, r, c, Op::C, j) && dbg::in_range(i, sl.ul, dbg::STATE))
+      this->u_out[c * sl.ul + i] = this->row(r, c)[j];
+  }
+  __device__ __forceinline__ void load_edge(int r, int c, int j, int64_t e) {
+    if (dbg::win(this->g.M, r, c, Op::C, j) && dbg::in_range(e, slab_edge_values(this->g, sl), dbg::EDGE))
+      this->row(r, c)[j] = this->e_in[e];
+  }
+  __device__ __forceinline__ void store_edge(int r, int c, int j, int64_t e) {
+    if (dbg::win(this->g.M, r, c, Op::C, j) && dbg::in_range(e, slab_edge_values(this->g, sl), dbg::EDGE))
+      this->e_out[e] = this->row(r, c)[j];
+  }
+};
+
+template <typename T, class Op, int P = 0>
+__global__ void SWEPT_BOUNDS(P, 1024) k_slab_up(Geom g, Slab sl, typename Op::K k, const T* u_in, T* u_out, T* e_out,
+                                                int hh, int write_top) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  auto cx = tiers_ctx<P>(
+      SlabCtx<T, Op>{{reinterpret_cast<T*>(smraw), g, k, u_in, u_out, nullptr, e_out, Tape<T>{}}, sl});
+  run_up(cx, g, sl.b0 + (int64_t)blockIdx.x, hh, write_top != 0);
+}
+
+template <typename T, class Op, int P = 0>
+__global__ void SWEPT_BOUNDS(P, 1024) k_slab_diamond(Geom g, Slab sl, typename Op::K k, T* u_out, const T* e_in,
+                                                     T* e_out, int odd, int mode, int hh) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  auto cx = tiers_ctx<P>(
+      SlabCtx<T, Op>{{reinterpret_cast<T*>(smraw), g, k, nullptr, u_out, e_in, e_out, Tape<T>{}}, sl});
+  run_diamond(cx, g, sl.b0 + (int64_t)blockIdx.x, odd, mode, hh);
+}
+
 // forward passes that also record every computed tier into a tape
 template <typename T, class Op>
 __global__ void __launch_bounds__(1024) k_swept_up_tape(Geom g, typename Op::K k, const T* u_in, T* u_out, T* e_out,

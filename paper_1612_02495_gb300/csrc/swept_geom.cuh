@@ -125,6 +125,32 @@ SW_HD int64_t edge_index(const Geom& g, int64_t tile, int side, int s, int c, in
   return tile * (int64_t)g.E + ((int64_t)(side * g.h + s) * g.C + c) * (2 * g.R) + k;
 }
 
+// A slab of a grid split over several ranks (the multi-GPU swept solver that
+// the paper names as future work, Section "Conclusion"): the nt tiles are
+// divided into contiguous runs, and a rank runs blocks [b0, b0 + nb) of every
+// pass.  Its state array holds global points [x0, x0 + ul) of each component
+// at index c ul + (x - x0), with no wrap-around: the blocks of an odd pass
+// reach W/2 points past the slab's end, which the right neighbour owns.  Its
+// edge buffers hold ns = min(nb + 2, nt) tile slots: the neighbours' tiles
+// b0 - 1 and b0 + nb (mod nt, "ghost" slots filled by the exchange) around
+// its own tiles, then the flat-top slot when X > 0.
+struct Slab {
+  int64_t b0 = 0, nb = 0;  // first block and number of blocks of this slab
+  int64_t x0 = 0, ul = 0;  // global point of state index 0; values per component
+  int64_t ns = 0;          // tile slots of each edge buffer (before the flat-top slot)
+};
+// slot of tile t (0 <= t < nt) in a slab's edge buffers: (t - b0 + 1) mod nt
+SW_HD int64_t slab_slot(const Geom& g, const Slab& sl, int64_t t) {
+  int64_t d = t - sl.b0 + 1;
+  if (d < 0) d += g.nt;
+  else if (d >= g.nt) d -= g.nt;
+  return d;
+}
+// values of one edge buffer of a slab
+SW_HD int64_t slab_edge_values(const Geom& g, const Slab& sl) {
+  return sl.ns * (int64_t)g.E + (g.X > 0 ? (int64_t)g.C * g.X : 0);
+}
+
 // pass p >= 1: boundary (diamond centre) handled by block b, and its two tiles
 SW_HD int64_t pass_center(const Geom& g, int odd, int64_t b) {
   return odd ? (b + 1) * (int64_t)g.W : b * (int64_t)g.W + g.W / 2;

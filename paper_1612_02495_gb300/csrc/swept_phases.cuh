@@ -15,10 +15,38 @@
 //                                  compute sub-timestep (base + s) on [lo, hi)
 //                                  into row s&1 from row (s-1)&1 (and row s&1
 //                                  for the second stage), then sync
+//   kSlab (optional, with member `sl`)
+//                                  the context runs one slab of a grid split
+//                                  over ranks: edge indices go to the slab's
+//                                  own slots (slab_slot)
 #pragma once
+#include <type_traits>
+
 #include "swept_geom.cuh"
 
 namespace swept {
+
+template <class Cx, class = void>
+struct is_slab_ctx : std::false_type {};
+template <class Cx>
+struct is_slab_ctx<Cx, std::enable_if_t<Cx::kSlab>> : std::true_type {};
+
+// offset of an edge value of `tile` (edge_index), in the context's edge buffers
+template <class Cx>
+SW_HD int64_t edge_at(const Cx& cx, const Geom& g, int64_t tile, int side, int s, int c, int k) {
+  if constexpr (is_slab_ctx<Cx>::value)
+    return edge_index(g, slab_slot(g, cx.sl, tile), side, s, c, k);
+  else
+    return edge_index(g, tile, side, s, c, k);
+}
+// offset of flat-top value k of component c (top_index), in the context's edge buffers
+template <class Cx>
+SW_HD int64_t top_at(const Cx& cx, const Geom& g, int c, int k) {
+  if constexpr (is_slab_ctx<Cx>::value)
+    return cx.sl.ns * (int64_t)g.E + (int64_t)c * g.X + k;
+  else
+    return top_index(g, c, k);
+}
 
 // f(s) for the tiers s = 1..n in order, two per trip: with a stage count that
 // is a compile-time constant (two-stage schemes alternate stages), each call's
@@ -59,7 +87,7 @@ SW_HD void run_up(Cx& cx, const Geom& g_in, int64_t b, int hh, bool write_top) {
     const int s = rem / per_level;
     const int c = (rem - s * per_level) / (2 * g.R);
     const int k = rem % (2 * g.R);
-    cx.store_edge(s & 1, c, edge_pos(g, side, s, k, w), edge_index(g, b, side, s, c, k));
+    cx.store_edge(s & 1, c, edge_pos(g, side, s, k, w), edge_at(cx, g, b, side, s, c, k));
   });
   if (write_top) {
     const int lo = g.R + g.R * hh, tw = w - 2 * g.R * hh;
@@ -72,7 +100,7 @@ SW_HD void run_up(Cx& cx, const Geom& g_in, int64_t b, int hh, bool write_top) {
     const int lo = g.R + g.W / 2;
     cx.for_range(0, g.X * g.C, [&](int i) {
       const int c = g.C == 1 ? 0 : i / g.X, k = i - c * g.X;
-      cx.store_edge(g.h & 1, c, lo + k, top_index(g, c, k));
+      cx.store_edge(g.h & 1, c, lo + k, top_at(cx, g, c, k));
     });
   }
 }
@@ -111,13 +139,13 @@ SW_HD void run_diamond(Cx& cx, const Geom& g_in, int64_t b, int odd, int mode, i
     const int k = rem % (2 * g.R);
     const int side = which == 0 ? 1 : 0;
     const int64_t tile = which == 0 ? tl : tr;
-    cx.load_edge(s & 1, cc, dofs + insert_pos(g, side, s, k), edge_index(g, tile, side, s, cc, k));
+    cx.load_edge(s & 1, cc, dofs + insert_pos(g, side, s, k), edge_at(cx, g, tile, side, s, cc, k));
   });
   if (wide) {
     const int lo = odd ? g.R : g.R + g.W;
     cx.for_range(0, g.X * g.C, [&](int i) {
       const int cc = g.C == 1 ? 0 : i / g.X, k = i - cc * g.X;
-      cx.load_edge(g.h & 1, cc, lo + k, top_index(g, cc, k));
+      cx.load_edge(g.h & 1, cc, lo + k, top_at(cx, g, cc, k));
     });
   }
   cx.sync();
@@ -133,13 +161,13 @@ SW_HD void run_diamond(Cx& cx, const Geom& g_in, int64_t b, int odd, int mode, i
       const int s = rem / per_level;
       const int cc = (rem - s * per_level) / (2 * g.R);
       const int k = rem % (2 * g.R);
-      cx.store_edge(s & 1, cc, edge_pos(g, side, s, k, w), edge_index(g, b, side, s, cc, k));
+      cx.store_edge(s & 1, cc, edge_pos(g, side, s, k, w), edge_at(cx, g, b, side, s, cc, k));
     });
     if (wide) {
       const int lo = g.R + g.W / 2;
       cx.for_range(0, g.X * g.C, [&](int i) {
         const int cc = g.C == 1 ? 0 : i / g.X, k = i - cc * g.X;
-        cx.store_edge(g.h & 1, cc, lo + k, top_index(g, cc, k));
+        cx.store_edge(g.h & 1, cc, lo + k, top_at(cx, g, cc, k));
       });
     }
   } else if (mode == MODE_DOWN) {

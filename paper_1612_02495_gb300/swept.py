@@ -563,3 +563,311 @@ def debug_status():
     if st == SWEPT_EDEVICE:
         return bool(en.value), (DEBUG_CHECK_NAMES.get(chk.value, str(chk.value)), idx.value)
     raise SweptError(st, "swept_debug_status")
+
+
+# ---------------------------------------------------------------------------
+# one grid split over ranks (include/swept_slab.h): the multi-GPU swept solver
+# ---------------------------------------------------------------------------
+class swept_slab_layout(ctypes.Structure):
+    _fields_ = [("first_block", _I64), ("blocks", _I64), ("x0", _I64), ("x1", _I64), ("state_len", _I64),
+                ("edge_values", _I64), ("e0_offset", _I64), ("e1_offset", _I64), ("workspace_bytes", _I64),
+                ("tile_w", _I32), ("threads", _I32), ("half_cycle", _I32), ("value_bytes", _I32)]
+
+
+class swept_slab_xfer(ctypes.Structure):
+    _fields_ = [("peer", _I32), ("recv", _I32), ("region", _I32), ("reserved", _I32), ("offset", _I64),
+                ("count", _I64)]
+
+
+swept_slab_init = _sig("swept_slab_init", [ctypes.POINTER(swept_config), _I32, _I32, ctypes.POINTER(_H)])
+swept_slab_get_layout = _sig("swept_slab_get_layout", [_H, ctypes.POINTER(swept_slab_layout)])
+swept_slab_bind_workspace = _sig("swept_slab_bind_workspace", [_H, _P, _SZ])
+swept_slab_launch_count = _sig("swept_slab_launch_count", [_H, _I64, ctypes.POINTER(_I64)])
+swept_slab_launch = _sig("swept_slab_launch", [_H, _P, _I64, _I64, _P])
+swept_slab_xfers = _sig("swept_slab_xfers", [_H, _I64, _I64, ctypes.POINTER(swept_slab_xfer), _I32,
+                                             ctypes.POINTER(_I32)])
+swept_slab_last_error = _sig("swept_slab_last_error", [_H, ctypes.c_char_p, _SZ])
+swept_slab_free = _sig("swept_slab_free", [_H], None)
+swept_slab_check = _sig("swept_slab_check", [ctypes.POINTER(swept_config), _I32, _I64, ctypes.POINTER(_I64),
+                                             ctypes.c_char_p, _SZ])
+swept_slab_sym_init = _sig("swept_slab_sym_init", [ctypes.POINTER(swept_config), _I32, _I32, _I64,
+                                                   ctypes.POINTER(_H)])
+swept_slab_sym_buffer = _sig("swept_slab_sym_buffer", [_H, _I32, ctypes.POINTER(ctypes.POINTER(_I64)),
+                                                       ctypes.POINTER(_I64)])
+swept_slab_sym_launch = _sig("swept_slab_sym_launch", [_H, _I64, ctypes.c_char_p, _SZ])
+swept_slab_sym_finish = _sig("swept_slab_sym_finish", [_H, ctypes.POINTER(_I32), ctypes.c_char_p, _SZ])
+swept_slab_sym_free = _sig("swept_slab_sym_free", [_H], None)
+
+REGION_E0, REGION_E1, REGION_STATE = 0, 1, 2
+
+
+def slab_check(scheme, dtype, n, dx, dt, param0, nranks, nsteps, bc=BC_PERIODIC, tile_w=0, threads=0, chunk=0,
+               warp_tiles=0):
+    """swept_slab_check: host-only symbolic replay of a solve split over nranks ranks; returns the
+    point updates performed, raises SweptError with the first violation."""
+    cfg = make_config(scheme, dtype, n, dx, dt, param0, bc, tile_w, threads, chunk, 0, 0, warp_tiles)
+    done = _I64()
+    msg = ctypes.create_string_buffer(512)
+    st = swept_slab_check(ctypes.byref(cfg), int(nranks), int(nsteps), ctypes.byref(done), msg, 512)
+    if st != SWEPT_OK:
+        raise SweptError(st, "swept_slab_check: " + msg.value.decode(errors="replace"))
+    return done.value
+
+
+def _slab_xfer_list(fn, h, nsteps, i):
+    buf = (swept_slab_xfer * 8)()
+    n = _I32()
+    st = fn(h, int(nsteps), int(i), buf, 8, ctypes.byref(n))
+    if st != SWEPT_OK:
+        raise SweptError(st, "swept_slab_xfers")
+    return [(x.peer, x.recv, x.region, x.offset, x.count) for x in buf[:n.value]]
+
+
+class Slab:
+    """Rank `rank` of a grid of n points split over `nranks` ranks, on the current CUDA device.
+
+    The rank's state is a contiguous tensor of C * layout["state_len"] values (C = 3 for
+    Euler): global points [x0, x0 + state_len) of each component; the rank owns [x0, x1)
+    before and after a solve.  `step` runs the rank's launches and, after each, hands the
+    listed transfers to `transport(xfers, views, launch_index)`, where views[region] is the
+    flat tensor a transfer's offset and count index (edge buffer 0, 1, the state)."""
+
+    def __init__(self, scheme, dtype, n, dx, dt, param0, rank, nranks, bc=BC_PERIODIC, tile_w=0, threads=0,
+                 chunk=0, warp_tiles=0):
+        import torch
+
+        self.cfg = make_config(scheme, dtype, n, dx, dt, param0, bc, tile_w, threads, chunk, 0, 0, warp_tiles)
+        h = _H()
+        st = swept_slab_init(ctypes.byref(self.cfg), int(rank), int(nranks), ctypes.byref(h))
+        if st != SWEPT_OK:
+            raise SweptError(st, "swept_slab_init rejected the configuration")
+        self.h = h.value
+        self.rank, self.nranks, self.n, self.scheme = int(rank), int(nranks), int(n), scheme
+        self.C = 3 if scheme == EULER else 1
+        self.torch_dtype = torch.float32 if dtype == F32 else torch.float64
+        lay = swept_slab_layout()
+        self._check(swept_slab_get_layout(self.h, ctypes.byref(lay)), "swept_slab_get_layout")
+        self.layout = {f: getattr(lay, f) for f, _ in lay._fields_}
+        self.ws = torch.empty(int(lay.workspace_bytes), dtype=torch.uint8, device="cuda")
+        self._check(swept_slab_bind_workspace(self.h, ctypes.c_void_p(self.ws.data_ptr()), int(lay.workspace_bytes)),
+                    "swept_slab_bind_workspace")
+        flat = self.ws.view(self.torch_dtype)
+        ev = int(lay.edge_values)
+        self._edges = [flat[lay.e0_offset:lay.e0_offset + ev], flat[lay.e1_offset:lay.e1_offset + ev]]
+
+    def _check(self, st, what):
+        if st != SWEPT_OK:
+            buf = ctypes.create_string_buffer(512)
+            swept_slab_last_error(self.h, buf, 512)
+            raise SweptError(st, what + ": " + buf.value.decode(errors="replace"))
+
+    def local_state(self, u_global):
+        """This rank's state array cut from a whole field (C * n values, any device)."""
+        import torch
+
+        L = self.layout
+        x0, x1, ul = L["x0"], L["x1"], L["state_len"]
+        g = u_global.reshape(self.C, self.n)
+        u = torch.zeros(self.C, ul, dtype=self.torch_dtype, device="cuda")
+        u[:, :x1 - x0] = g[:, x0:x1].to(device="cuda", dtype=self.torch_dtype)
+        return u.reshape(-1).contiguous()
+
+    def owned(self, u_local):
+        """The rank's points [x0, x1) of its state array, shape (C, x1 - x0)."""
+        L = self.layout
+        return u_local.reshape(self.C, L["state_len"])[:, :L["x1"] - L["x0"]]
+
+    def launch_count(self, nsteps):
+        c = _I64()
+        self._check(swept_slab_launch_count(self.h, int(nsteps), ctypes.byref(c)), "swept_slab_launch_count")
+        return c.value
+
+    def xfers(self, nsteps, i):
+        return _slab_xfer_list(swept_slab_xfers, self.h, nsteps, i)
+
+    def views(self, u_local):
+        return [self._edges[0], self._edges[1], u_local]
+
+    def launch(self, u_local, nsteps, i, stream=None):
+        if not u_local.is_cuda or not u_local.is_contiguous() or u_local.dtype != self.torch_dtype or \
+                u_local.numel() != self.C * self.layout["state_len"]:
+            raise ValueError("u_local must be the rank's contiguous state array (C * state_len values)")
+        self._check(swept_slab_launch(self.h, ctypes.c_void_p(u_local.data_ptr()), int(nsteps), int(i),
+                                      _stream_ptr(stream)), "swept_slab_launch")
+
+    def step(self, u_local, nsteps, transport, stream=None):
+        """Advance the rank's state nsteps timesteps, trading with its neighbours through `transport`."""
+        for i in range(self.launch_count(nsteps)):
+            self.launch(u_local, nsteps, i, stream)
+            xs = self.xfers(nsteps, i)
+            if xs:
+                transport(xs, self.views(u_local), i)
+        return u_local
+
+    def close(self):
+        if getattr(self, "h", None):
+            swept_slab_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SlabSym:
+    """The symbolic replay of one rank (swept_slab_sym_*): the same launches and transfers as
+    `Slab`, over buffers of (point, sub-timestep) tags, two int64 per value.  views() are torch
+    int64 CPU tensors of shape (values, 2) sharing the replay's memory, so a transport moves
+    rows [offset, offset + count) exactly as it moves values on the GPU."""
+
+    def __init__(self, scheme, dtype, n, dx, dt, param0, rank, nranks, nsteps, bc=BC_PERIODIC, tile_w=0, threads=0,
+                 chunk=0, warp_tiles=0):
+        import numpy as np
+        import torch
+
+        cfg = make_config(scheme, dtype, n, dx, dt, param0, bc, tile_w, threads, chunk, 0, 0, warp_tiles)
+        h = _H()
+        st = swept_slab_sym_init(ctypes.byref(cfg), int(rank), int(nranks), int(nsteps), ctypes.byref(h))
+        if st != SWEPT_OK:
+            raise SweptError(st, "swept_slab_sym_init rejected the configuration")
+        self.h = h.value
+        self.nsteps = int(nsteps)
+        # the launch count and transfer lists come from a slab handle of the same configuration
+        ph = _H()
+        check(swept_slab_init(ctypes.byref(cfg), int(rank), int(nranks), ctypes.byref(ph)), None, "swept_slab_init")
+        self._ph = ph.value
+        self._views = []
+        for region in range(3):
+            p = ctypes.POINTER(_I64)()
+            nv = _I64()
+            check(swept_slab_sym_buffer(self.h, region, ctypes.byref(p), ctypes.byref(nv)), None,
+                  "swept_slab_sym_buffer")
+            a = np.ctypeslib.as_array(p, shape=(int(nv.value), 2)) if nv.value else np.zeros((0, 2), np.int64)
+            self._views.append(torch.from_numpy(a))
+        self.n = int(n)
+
+    def launch_count(self, nsteps):
+        c = _I64()
+        check(swept_slab_launch_count(self._ph, int(nsteps), ctypes.byref(c)), None, "swept_slab_launch_count")
+        return c.value
+
+    def xfers(self, nsteps, i):
+        return _slab_xfer_list(swept_slab_xfers, self._ph, nsteps, i)
+
+    def views(self, u_local=None):
+        return self._views
+
+    def launch(self, u_local, nsteps, i, stream=None):
+        msg = ctypes.create_string_buffer(512)
+        st = swept_slab_sym_launch(self.h, int(i), msg, 512)
+        if st != SWEPT_OK:
+            raise SweptError(st, "swept_slab_sym_launch: " + msg.value.decode(errors="replace"))
+
+    def step(self, u_local, nsteps, transport, stream=None):
+        return Slab.step(self, u_local, nsteps, transport, stream)
+
+    def finish(self, counts):
+        """Check the rank's final state; add its per-(sub-timestep, point) update counts into
+        `counts` (a contiguous int32 numpy array of (nsteps S + 1) * n entries)."""
+        msg = ctypes.create_string_buffer(512)
+        st = swept_slab_sym_finish(self.h, counts.ctypes.data_as(ctypes.POINTER(_I32)), msg, 512)
+        if st != SWEPT_OK:
+            raise SweptError(st, "swept_slab_sym_finish: " + msg.value.decode(errors="replace"))
+
+    def close(self):
+        if getattr(self, "h", None):
+            swept_slab_sym_free(self.h)
+            self.h = None
+        if getattr(self, "_ph", None):
+            swept_slab_free(self._ph)
+            self._ph = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _pair_keys(xs):
+    """(direction of travel, ordinal) of each transfer: a send to side p travels p, a receive
+    from side p travels -p; the k-th message of one direction between two neighbours pairs the
+    k-th send with the k-th receive."""
+    seen = {}
+    keys = []
+    for peer, recv, region, offset, count in xs:
+        travel = -peer if recv else peer
+        k = seen.get((travel, recv), 0)
+        seen[(travel, recv)] = k + 1
+        keys.append((travel, k))
+    return keys
+
+
+def dist_transport(group=None):
+    """A transport over torch.distributed point-to-point messages (NCCL between GPUs, gloo on the
+    host): every transfer after one launch is posted in one batch_isend_irecv, in the same
+    (direction, ordinal) order on both ends of each message, and waited for before the next
+    launch.  One rank (world size 1) copies its sends into its own receives."""
+    import torch.distributed as dist
+
+    rank = dist.get_rank(group)
+    world = dist.get_world_size(group)
+
+    def transport(xs, views, i):
+        keys = _pair_keys(xs)
+        if world == 1:
+            return local_copy([(xs, views)], [keys])
+        ops = []
+        order = sorted(range(len(xs)), key=lambda j: keys[j])
+        for j in order:
+            peer, recv, region, offset, count = xs[j]
+            travel, k = keys[j]
+            v = views[region][offset:offset + count]
+            tag = (int(i) * 2 + (0 if travel > 0 else 1)) * 16 + k
+            dst = (rank + peer) % world
+            if group is not None:
+                dst = dist.get_global_rank(group, dst)
+            ops.append(dist.P2POp(dist.irecv if recv else dist.isend, v, dst, group, tag))
+        for w in dist.batch_isend_irecv(ops):
+            w.wait()
+
+    return transport
+
+
+def local_copy(rank_xfers, rank_keys=None):
+    """Carry out the transfers of ranks that live in one process (rank_xfers[r] = (xfers, views)
+    of rank r, in ring order): each send is copied into the receive it pairs with."""
+    R = len(rank_xfers)
+    keys = rank_keys or [_pair_keys(xs) for xs, _ in rank_xfers]
+    for r, (xs, views) in enumerate(rank_xfers):
+        for j, (peer, recv, region, offset, count) in enumerate(xs):
+            if recv:
+                continue
+            q = (r + peer) % R
+            qxs, qviews = rank_xfers[q]
+            for jj, (qpeer, qrecv, qregion, qoffset, qcount) in enumerate(qxs):
+                if qrecv and qpeer == -peer and keys[q][jj] == keys[r][j]:
+                    if qcount != count:
+                        raise RuntimeError("paired transfers differ in size")
+                    src = views[region][offset:offset + count]
+                    dst = qviews[qregion][qoffset:qoffset + qcount]
+                    if src.data_ptr() != dst.data_ptr():
+                        dst.copy_(src.clone() if q == r else src)
+                    break
+            else:
+                raise RuntimeError("a send of rank %d has no matching receive" % r)
+
+
+def run_slabs_local(slabs, states, nsteps, stream=None):
+    """All ranks of a split grid in one process (one GPU, one stream): launch i on every rank,
+    then the transfers after it as device copies.  For testing the partition on one device."""
+    n = slabs[0].launch_count(nsteps)
+    for i in range(n):
+        for s, u in zip(slabs, states):
+            s.launch(u, nsteps, i, stream)
+        lists = [(s.xfers(nsteps, i), s.views(u)) for s, u in zip(slabs, states)]
+        if any(xs for xs, _ in lists):
+            local_copy(lists)
+    return states
