@@ -45,11 +45,12 @@ FP64_KS_MIX_CEILING = 0.535e12
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_swept_diamond<double, KsOp> launch at
 # N = 2^20, tile 1024, from an ncu capture; None: no capture of the current kernel
 DIAMOND_TRAFFIC_BYTES = None
-# the same for one k_swept_persist<double, KsOp> launch (a whole 50,000-step solve) of the plan
-# (tile, threads) below: 11.56 MB read + 36.78 MB written in an ncu capture of just those two
-# counters and the duration, on the current kernel; reported only when the tuned plan is that plan
-PERSIST_TRAFFIC_BYTES = 48339456
-PERSIST_TRAFFIC_PLAN = (1024, 512)  # (tile, threads) of that capture
+# the same for one k_swept_persist<double, KsOp> launch (a whole 50,000-step solve), per plan
+# (tile, threads): dram__bytes_read.sum + dram__bytes_write.sum from an ncu capture of just those
+# two counters and the duration, on the current kernel (tile 1024 / 512 threads: 11.56 MB read +
+# 36.78 MB written; tile 1024 / 256 threads: 9.23 MB + 5.75 MB); a plan without a capture
+# reports None
+PERSIST_TRAFFIC = {(1024, 512): 48339456, (1024, 256): 9232128 + 5747968}
 
 
 # Measured unit ceilings of GB300 (python -m paper_1612_02495_gb300.peaks, register-only probe loops):
@@ -612,17 +613,16 @@ def main():
         # memsets and a one-thread status kernel)
         units = N * 2 * NSTEPS
         roofline = {"bound": "alu", "achieved": FP64_FLOPS_PER_SUBSTEP * units / (ms * 1e-3) / 1e12,
-                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "traffic": PERSIST_TRAFFIC_BYTES,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "traffic": None if plan.get("warp_tiles") else PERSIST_TRAFFIC.get((plan["tile_w"], plan["threads"])),
                     "kernel": "k_swept_persist<double, KsOp<double>%s>" % (
                         ", %d" % (plan["tile_w"] // 32) if plan.get("warp_tiles") else ""), "peak_source": peak_src,
                     "pipe_frac": FP64_INSTR_PER_SUBSTEP * units / (ms * 1e-3) / FP64_INSTR_PEAK,
                     "frac_of_measured_mix_ceiling": FP64_INSTR_PER_SUBSTEP * units / (ms * 1e-3) / FP64_KS_MIX_CEILING,
                     "kernel_ms_avg": ms, "kernel_share": 1.0}
-        if (plan["tile_w"], plan["threads"]) != PERSIST_TRAFFIC_PLAN or plan.get("warp_tiles"):
-            roofline["traffic"] = None  # the ncu figure is for another plan
-        else:
-            roofline["traffic_note"] = "ncu capture of this plan's persistent launch (tile 1024, 512 threads), " \
-                                       "50,000 steps"
+        if roofline["traffic"] is not None:
+            roofline["traffic_note"] = "ncu capture of this plan's persistent launch (tile %d, %d threads), " \
+                                       "50,000 steps" % (plan["tile_w"], plan["threads"])
         roofline["frac"] = roofline["achieved"] / FP64_PEAK_TFLOPS
         launches_per_step = 2
     else:

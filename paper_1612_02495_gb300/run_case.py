@@ -6,6 +6,9 @@
       (the batched workload: count heat/KS problems, N = 2^U(10,18) rounded to 1024, 1,000-20,000 steps)
   python -m paper_1612_02495_gb300.run_case --scheme ks --adjoint 1 --n 262144 --nsteps 5000
       (FP64 heat / KS: the checkpointing forward solve, then the reverse sweep; times both)
+  python -m paper_1612_02495_gb300.run_case --scheme ks --slab 2 --n 1048576 --nsteps 1000 --tile 1024
+      (the grid split over --slab ranks, all in this process on one GPU: every rank's launch i, then
+      the transfers after it as device copies; checks the gathered result against swept_step_n)
 
 Used to profile a single kernel on a chosen size (e.g. under ncu).  One
 untimed warm-up solve precedes the timed repeats.
@@ -33,6 +36,7 @@ def main(argv=None):
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--count", type=int, default=4096, help="batch: number of problems")
     ap.add_argument("--adjoint", type=int, default=0, help="heat / KS FP64: time the adjoint sweep")
+    ap.add_argument("--slab", type=int, default=0, help="split the grid over this many ranks (one process)")
     a = ap.parse_args(argv)
 
     import torch
@@ -60,6 +64,8 @@ def main(argv=None):
         p = inputs.euler_problem(n=a.n, dtype=npd)
         args = (S.EULER, dt_code, a.n, p["dx"], p["dt"], p["gamma"], S.BC_REFLECTIVE)
         u0 = p["U0"]
+    if a.slab:
+        return run_slab(a, S, torch, args, u0)
     sol = S.Solver(*args, tile_w=a.tile, threads=a.threads, chunk=a.chunk, persistent=a.persistent,
                    cluster=a.cluster, warp_tiles=a.warp_tiles)
     u_init = torch.from_numpy(np.ascontiguousarray(u0)).cuda()
@@ -83,6 +89,40 @@ def main(argv=None):
                       "cell_updates_per_s": a.n * a.nsteps / (ms * 1e-3)}))
     sol.close()
     return 0
+
+
+def run_slab(a, S, torch, args, u0):
+    """The grid split over a.slab ranks in one process, against the whole-grid per-pass solve."""
+    scheme, dt_code, n, dx, dt, p0, bc = args
+    slabs = [S.Slab(scheme, dt_code, n, dx, dt, p0, r, a.slab, bc=bc, tile_w=a.tile, threads=a.threads,
+                    chunk=a.chunk, warp_tiles=a.warp_tiles) for r in range(a.slab)]
+    ug = torch.from_numpy(np.ascontiguousarray(u0))
+    states = [s.local_state(ug) for s in slabs]
+    init = [u.clone() for u in states]
+    S.run_slabs_local(slabs, states, a.nsteps)
+    torch.cuda.synchronize()
+
+    def solve():
+        for u, v in zip(states, init):
+            u.copy_(v)
+        S.run_slabs_local(slabs, states, a.nsteps)
+
+    ms = _event_ms(torch, solve, a.repeat)
+    got = torch.cat([s.owned(u) for s, u in zip(slabs, states)], dim=1).reshape(-1)
+    sol = S.Solver(scheme, dt_code, n, dx, dt, p0, bc, tile_w=a.tile, threads=a.threads, chunk=a.chunk,
+                   warp_tiles=a.warp_tiles)
+    u = ug.cuda()
+    whole_ms = _event_ms(torch, lambda: (u.copy_(ug.cuda()), sol.step(u, a.nsteps)), a.repeat)
+    torch.cuda.synchronize()
+    same = bool(torch.equal(got, u.reshape(-1)))
+    print(json.dumps({"scheme": a.scheme, "dtype": a.dtype, "n": n, "nsteps": a.nsteps, "ranks": a.slab,
+                      "layout": [s.layout for s in slabs], "ms": ms, "whole_grid_ms": whole_ms,
+                      "launches_per_rank": slabs[0].launch_count(a.nsteps), "equal_to_whole_grid": same,
+                      "cell_updates_per_s": n * a.nsteps / (ms * 1e-3)}))
+    for s in slabs:
+        s.close()
+    sol.close()
+    return 0 if same else 1
 
 
 def run_heat2d(a, S, inputs, torch, npd, dt_code):
