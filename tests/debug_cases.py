@@ -7,6 +7,7 @@ Every execution mode of every kernel family runs on small seeded cases:
     are not a multiple of the tile width;
   - classic;
   - the batched solver, the adjoint, the no-allocation entry point;
+  - a grid split over ranks (all ranks in this process), every scheme;
   - 2D per pass and persistent, both boundary conditions.
 After each group the debug records must be clean (swept_debug_status), and
 every result must equal the oracle bit for bit.  Prints one line per group and
@@ -153,6 +154,32 @@ def main():
         assert np.array_equal(g.cpu().numpy(), ref), ("adjoint", sc)
         sol.close()
     clean("adjoint")
+
+    # a grid split over ranks: every rank's state and edge indices checked on the device
+    for sc, n, W, nsteps, bc, nranks, extra in [(S.HEAT, 1009, 32, 203, 1, 3, {}), (S.HEAT, 1024, 64, 99, 0, 2,
+                                                                                      {"warp_tiles": 1}),
+                                                (S.KS, 4099, 128, 97, 0, 4, {}), (S.EULER, 1024, 64, 55, 1, 3, {})]:
+        if sc == S.HEAT:
+            p = inputs.heat_problem(n=n)
+            u0, args = p["u0"], (p["dx"], p["dt"], p["alpha"])
+            ref = oracle.heat(u0, *args, nsteps, bc=bc)
+        elif sc == S.KS:
+            p = inputs.ks_problem(n=n)
+            u0, args = p["u0"], (p["dx"], p["dt"], p["nu"])
+            ref = oracle.ks(u0, *args, nsteps, threads=8)
+        else:
+            pr = inputs.euler_problem(n=n)
+            u0, args = pr["U0"], (pr["dx"], pr["dt"], pr["gamma"])
+            ref = oracle.euler(u0, *args, nsteps, bc=bc, threads=8)
+        slabs = [S.Slab(sc, S.F64, n, *args, r, nranks, bc=bc, tile_w=W, **extra) for r in range(nranks)]
+        states = [s.local_state(torch.from_numpy(np.ascontiguousarray(u0))) for s in slabs]
+        S.run_slabs_local(slabs, states, nsteps)
+        torch.cuda.synchronize()
+        got = np.concatenate([s.owned(u).cpu().numpy() for s, u in zip(slabs, states)], axis=1)
+        assert np.array_equal(got.reshape(-1), np.asarray(ref).reshape(-1)), ("slab", sc, n, nranks)
+        for s in slabs:
+            s.close()
+    clean("slabs")
 
     # 2D, per pass and persistent, both boundary conditions
     for dtype in (np.float64, np.float32):
