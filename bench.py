@@ -309,6 +309,47 @@ def measure_fp32(S, inputs, autotune, torch, stream, barrier, ws):
             "speedup_vs_classic": res["classic"] / res["swept"], "roofline": rf}
 
 
+def measure_slab(S, inputs, torch, stream, barrier, ranks=(2, 8), nsteps=2000, W=1024, threads=256):
+    """The KS 2^20 FP64 grid split over several ranks, all of them in this process on this GPU
+    (launch i of every rank, then the transfers after it as device copies), against the
+    whole-grid solve with one launch per pass; each split result must equal the whole grid."""
+    p = inputs.ks_problem(n=N)
+    ug = torch.from_numpy(p["u0"])
+    sol = S.Solver(S.KS, S.F64, N, p["dx"], p["dt"], p["nu"], tile_w=W, threads=threads)
+    u = ug.cuda()
+    sol.step(u, nsteps)
+    barrier()
+    u.copy_(ug)
+    ev = _event_time(torch, stream, lambda: sol.step(u, nsteps))
+    barrier()
+    whole_ms = ev[0].elapsed_time(ev[1])
+    sol.sync_status()
+    sol.close()
+    rows = []
+    for R in ranks:
+        slabs = [S.Slab(S.KS, S.F64, N, p["dx"], p["dt"], p["nu"], r, R, tile_w=W, threads=threads)
+                 for r in range(R)]
+        states = [s.local_state(ug) for s in slabs]
+        init = [x.clone() for x in states]
+        S.run_slabs_local(slabs, states, nsteps)
+        barrier()
+        for x, y in zip(states, init):
+            x.copy_(y)
+        ev = _event_time(torch, stream, lambda: S.run_slabs_local(slabs, states, nsteps))
+        barrier()
+        got = torch.cat([s.owned(x) for s, x in zip(slabs, states)], dim=1).reshape(-1)
+        rows.append({"ranks": R, "ms": ev[0].elapsed_time(ev[1]), "equal_to_whole_grid": bool(torch.equal(got, u)),
+                     "launches_per_rank": slabs[0].launch_count(nsteps),
+                     "transfer_values_per_pass": slabs[0].layout["half_cycle"] * 2 * 2})
+        for s in slabs:
+            s.close()
+    return {"workload": "KS N=2^20 FP64, %d steps, split over ranks that all run on this one GPU "
+                        "(tile %d, %d threads)" % (nsteps, W, threads),
+            "whole_grid_ms": whole_ms, "splits": rows,
+            "note": "one GPU runs every rank in turn, so this checks the partition and its launch cost, "
+                    "not multi-GPU throughput"}
+
+
 def measure_batch(S, inputs, autotune, torch, stream, barrier, ws, with_f64):
     """Batched workload: 4096 heat/KS problems, N = 2^U(10,18) rounded to 1024,
     1,000-20,000 steps, one persistent launch per run; FP32 (and FP64 on request)."""
@@ -525,6 +566,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-sizes", action="store_true")
     ap.add_argument("--no-2d", action="store_true")
+    ap.add_argument("--no-slab", action="store_true", help="skip the split-grid line")
     ap.add_argument("--no-batch-f64", action="store_true", help="skip the FP64 batch (about 2 x 50 s)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -656,6 +698,9 @@ def main():
     heat2d = None
     if not args.no_2d:
         heat2d = measure_heat2d(S, autotune, torch, stream, barrier, ws, flush)
+    slab = None
+    if not args.no_slab:
+        slab = measure_slab(S, inputs, torch, stream, barrier)
     batched = None
     if not args.no_batch:
         batched = measure_batch(S, inputs, autotune, torch, stream, barrier, ws, not args.no_batch_f64)
@@ -680,6 +725,8 @@ def main():
         out["sizes"] = sizes
     if heat2d:
         out["heat2d"] = heat2d
+    if slab:
+        out["slab"] = slab
     out["config"]["autotuned"] = {k: tuned.get(k, 0) for k in ("tile_w", "threads", "warp_tiles", "persistent",
                                                                 "cluster")}
     if ms_classic:
