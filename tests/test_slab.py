@@ -252,3 +252,42 @@ def test_gloo_ranks_carry_the_exchange(S, world, case):
     for rank, status, a, b in res:
         assert status == "ok", (rank, a)
         assert a == 1 and b == 1, (rank, a, b)
+
+
+def test_slab_calls_validate_before_touching_a_device(S):
+    """Error paths of the slab calls, on the host: no workspace, a launch index out of range,
+    a transfer list longer than the caller's array, NULL pointers; without a device a valid
+    launch fails with SWEPT_ECUDA instead of launching."""
+    import ctypes
+
+    cfg = S.make_config(S.EULER, S.F64, 1024, 1.0 / 1024, 1e-4, 1.4, bc=S.BC_REFLECTIVE, tile_w=64)
+    h = S._H()
+    assert S.swept_slab_init(ctypes.byref(cfg), 1, 3, ctypes.byref(h)) == S.SWEPT_OK
+    h = h.value
+    fake = ctypes.c_void_p(1 << 20)  # aligned, never dereferenced on these paths
+    assert S.swept_slab_launch(h, fake, 10, 0, None) == S.SWEPT_ENOWORKSPACE
+    assert S.swept_slab_launch(h, None, 10, 0, None) == S.SWEPT_EINVAL
+    assert S.swept_slab_bind_workspace(h, ctypes.c_void_p(1 << 20 | 8), 1 << 30) == S.SWEPT_EINVAL  # misaligned
+    lay = S.swept_slab_layout()
+    assert S.swept_slab_get_layout(h, ctypes.byref(lay)) == S.SWEPT_OK
+    assert S.swept_slab_bind_workspace(h, fake, lay.workspace_bytes - 1) == S.SWEPT_ENOMEM_WORKSPACE
+    assert S.swept_slab_bind_workspace(h, fake, lay.workspace_bytes) == S.SWEPT_OK
+    cnt = S._I64()
+    assert S.swept_slab_launch_count(h, 10, ctypes.byref(cnt)) == S.SWEPT_OK and cnt.value > 0
+    assert S.swept_slab_launch(h, fake, 10, cnt.value, None) == S.SWEPT_EINVAL
+    assert S.swept_slab_launch(h, fake, 10, -1, None) == S.SWEPT_EINVAL
+    assert S.swept_slab_launch(h, fake, -1, 0, None) == S.SWEPT_EINVAL
+    buf = (S.swept_slab_xfer * 8)()
+    n = S._I32()
+    # 10 Euler steps with h = 16: 20 sub-steps, one odd down pass and a remainder of 4; after the down
+    # pass and after the gap pass each of the 3 components is sent and received
+    worst = max(range(cnt.value), key=lambda i: len(S._slab_xfer_list(S.swept_slab_xfers, h, 10, i)))
+    m = len(S._slab_xfer_list(S.swept_slab_xfers, h, 10, worst))
+    assert m >= 2
+    assert S.swept_slab_xfers(h, 10, worst, buf, m - 1, ctypes.byref(n)) == S.SWEPT_EINVAL
+    assert S.swept_slab_xfers(h, 10, worst, None, 8, ctypes.byref(n)) == S.SWEPT_EINVAL
+    assert S.swept_slab_xfers(h, 10, cnt.value + 5, buf, 8, ctypes.byref(n)) == S.SWEPT_OK and n.value == 0
+    if not __import__("torch").cuda.is_available():
+        assert S.swept_slab_launch(h, fake, 10, 0, None) == S.SWEPT_ECUDA
+    S.swept_slab_free(h)
+    S.swept_slab_free(None)
