@@ -809,7 +809,10 @@ def dist_transport(group=None):
     """A transport over torch.distributed point-to-point messages (NCCL between GPUs, gloo on the
     host): every transfer after one launch is posted in one batch_isend_irecv, in the same
     (direction, ordinal) order on both ends of each message, and waited for before the next
-    launch.  One rank (world size 1) copies its sends into its own receives."""
+    launch.  One rank (world size 1) copies its sends into its own receives.  The slab's rank
+    and nranks must be this process's rank and size in `group` (the default group if None).
+    With NCCL the messages run in stream order after the launch that produced them, and the
+    current stream waits for them before the next launch."""
     import torch.distributed as dist
 
     rank = dist.get_rank(group)
