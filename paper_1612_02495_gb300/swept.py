@@ -805,14 +805,17 @@ def _pair_keys(xs):
     return keys
 
 
-def dist_transport(group=None):
+def dist_transport(group=None, stage_on_host=False):
     """A transport over torch.distributed point-to-point messages (NCCL between GPUs, gloo on the
     host): every transfer after one launch is posted in one batch_isend_irecv, in the same
     (direction, ordinal) order on both ends of each message, and waited for before the next
     launch.  One rank (world size 1) copies its sends into its own receives.  The slab's rank
     and nranks must be this process's rank and size in `group` (the default group if None).
     With NCCL the messages run in stream order after the launch that produced them, and the
-    current stream waits for them before the next launch."""
+    current stream waits for them before the next launch.  stage_on_host=True moves each message
+    through host memory (device to host before a send, host to device after a receive), for a
+    host backend such as gloo between processes whose ranks hold device buffers."""
+    import torch
     import torch.distributed as dist
 
     rank = dist.get_rank(group)
@@ -823,11 +826,17 @@ def dist_transport(group=None):
         if world == 1:
             return local_copy([(xs, views)], [keys])
         ops = []
+        staged = []
         order = sorted(range(len(xs)), key=lambda j: keys[j])
         for j in order:
             peer, recv, region, offset, count = xs[j]
             travel, k = keys[j]
             v = views[region][offset:offset + count]
+            if stage_on_host:
+                h = v.cpu() if not recv else torch.empty(v.shape, dtype=v.dtype)
+                if recv:
+                    staged.append((v, h))
+                v = h
             tag = (int(i) * 2 + (0 if travel > 0 else 1)) * 16 + k
             dst = (rank + peer) % world
             if group is not None:
@@ -835,6 +844,8 @@ def dist_transport(group=None):
             ops.append(dist.P2POp(dist.irecv if recv else dist.isend, v, dst, group, tag))
         for w in dist.batch_isend_irecv(ops):
             w.wait()
+        for v, h in staged:
+            v.copy_(h)
 
     return transport
 

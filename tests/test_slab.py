@@ -206,7 +206,7 @@ def _free_port():
     return p
 
 
-def _gloo_rank(rank, world, port, case, q):
+def _gloo_rank(rank, world, port, case, q, stage=False):
     try:
         import torch
         import torch.distributed as dist
@@ -219,7 +219,7 @@ def _gloo_rank(rank, world, port, case, q):
         scheme, bc, n, W, nsteps = case
         sym = S.SlabSym(scheme, S.F64, n, 0.1, 1e-3, 1.4 if scheme == S.EULER else 1.0, rank, world, nsteps, bc=bc,
                         tile_w=W)
-        sym.step(None, nsteps, S.dist_transport())
+        sym.step(None, nsteps, S.dist_transport(stage_on_host=stage))
         counts = np.zeros((nsteps * (1 if scheme == S.HEAT else 2) + 1) * n, dtype=np.int32)
         sym.finish(counts)
         t = torch.from_numpy(counts)
@@ -231,19 +231,20 @@ def _gloo_rank(rank, world, port, case, q):
         q.put((rank, "error", repr(e), None))
 
 
-@pytest.mark.parametrize("world,case", [
-    (2, (0, 0, 1024, 64, 101)),   # heat, periodic: odd down pass + remainder
-    (2, (1, 0, 2048, 128, 70)),   # KS
-    (3, (0, 1, 1009, 32, 77)),    # heat, insulated, ragged grid
-    (3, (2, 1, 1024, 64, 40)),    # Euler, reflective walls
+@pytest.mark.parametrize("world,case,stage", [
+    (2, (0, 0, 1024, 64, 101), False),   # heat, periodic: odd down pass + remainder
+    (2, (1, 0, 2048, 128, 70), False),   # KS
+    (3, (0, 1, 1009, 32, 77), False),    # heat, insulated, ragged grid
+    (3, (2, 1, 1024, 64, 40), False),    # Euler, reflective walls
+    (3, (1, 0, 1536, 128, 55), True),    # messages staged through host buffers
 ])
-def test_gloo_ranks_carry_the_exchange(S, world, case):
+def test_gloo_ranks_carry_the_exchange(S, world, case, stage):
     import multiprocessing as mp
 
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    ps = [ctx.Process(target=_gloo_rank, args=(r, world, port, case, q)) for r in range(world)]
+    ps = [ctx.Process(target=_gloo_rank, args=(r, world, port, case, q, stage)) for r in range(world)]
     for p in ps:
         p.start()
     res = [q.get(timeout=240) for _ in ps]

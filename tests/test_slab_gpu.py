@@ -111,3 +111,68 @@ def test_split_grid_two_solves_in_a_row(S):
     assert np.array_equal(got, ref_fn(u0, 333))
     for s in slabs:
         s.close()
+
+
+# --- ranks as processes, one GPU, messages through host memory --------------------------------
+
+def _free_port():
+    import socket
+
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _gpu_rank(rank, world, port, case, q):
+    try:
+        from datetime import timedelta
+
+        import torch.distributed as dist
+
+        os.environ["MASTER_ADDR"] = "127.0.0.1"
+        os.environ["MASTER_PORT"] = str(port)
+        torch.cuda.set_device(0)
+        dist.init_process_group("gloo", rank=rank, world_size=world, timeout=timedelta(seconds=120))
+        from paper_1612_02495_gb300 import swept as S
+
+        scheme, n, bc, W, nsteps = case
+        code, u0, args, ref_fn = problem(S, scheme, n, np.float64, bc)
+        slab = S.Slab(code, S.F64, n, *args, rank, world, bc=bc, tile_w=W)
+        u = slab.local_state(torch.from_numpy(np.ascontiguousarray(u0)))
+        slab.step(u, nsteps, S.dist_transport(stage_on_host=True))
+        torch.cuda.synchronize()
+        got = slab.owned(u).cpu().numpy()
+        x0, x1 = slab.layout["x0"], slab.layout["x1"]
+        ref = np.asarray(ref_fn(u0, nsteps)).reshape(-1, n)[:, x0:x1]
+        ok = bool(np.array_equal(got, ref))
+        slab.close()
+        dist.destroy_process_group()
+        q.put((rank, ok, "" if ok else "max abs diff %g" % float(np.max(np.abs(got - ref)))))
+    except Exception as e:  # reported to the parent
+        q.put((rank, False, repr(e)))
+
+
+@pytest.mark.parametrize("world,case", [
+    (2, ("ks", 1 << 14, 0, 256, 601)),
+    (3, ("heat", 1024, 1, 64, 333)),
+    (2, ("euler", 4096, 1, 128, 201)),
+])
+def test_ranks_as_processes_on_one_gpu(S, world, case):
+    """Each rank is its own process with its own CUDA context on the one GPU; the ranks trade
+    through a gloo process group with the messages staged in host memory (dist_transport), so
+    no kernel waits on another rank's kernel.  Every rank's points equal the oracle's."""
+    import multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_gpu_rank, args=(r, world, port, case, q)) for r in range(world)]
+    for p in ps:
+        p.start()
+    res = [q.get(timeout=600) for _ in ps]
+    for p in ps:
+        p.join(timeout=120)
+    for rank, ok, msg in res:
+        assert ok, (rank, msg)
