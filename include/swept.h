@@ -100,11 +100,13 @@ typedef enum {
  *            thread-block cluster; each block keeps its tile in shared memory
  *            for the whole solve and reads its neighbour's edges through
  *            distributed shared memory, with a cluster barrier between passes
- *   warp_tiles 1: heat and KS with tile_w = 32 P, P in {1, 2, 4, 8} (P >= 2 for
- *            KS): each tile is one warp (threads must be 0 or 32) whose lane l
- *            keeps points l P .. l P + P - 1 of the tier rows in registers and
- *            reads its stencil neighbours from lanes l - 1 and l + 1 by warp
- *            shuffle, so a tier needs no shared-memory access and no barrier.
+ *   warp_tiles 1: heat and KS with tile_w = 32 P, P in {1, 2, 4, 8}: each
+ *            tile is one warp (threads must be 0 or 32) whose lane l keeps
+ *            points l P .. l P + P - 1 of the tier rows in registers and reads
+ *            its stencil neighbours from the lanes beside it (up to ceil(r / P)
+ *            lanes away; KS with P = 1 is the paper's 32-point register node,
+ *            Section "Conclusion") by warp shuffle, so a tier needs no
+ *            shared-memory access and no barrier.
  *            Works with the per-pass, persistent and cluster modes; results are
  *            bit-identical to the shared-memory tiers.
  * Stability (Fo <= 1/2, CFL) is the caller's responsibility and is not checked.

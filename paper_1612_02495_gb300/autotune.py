@@ -102,10 +102,9 @@ def _time(fn, reps):
 
 def warp_tile_ok(scheme, W, n=None):
     """Tile widths the register (warp-tile) mapping supports: W = 32 P with
-    P in {1, 2, 4, 8} and at least r points per lane, dividing n; heat and KS only."""
+    P in {1, 2, 4, 8}, dividing n; heat and KS only."""
     P = W // 32
-    return (scheme != S.EULER and W % 32 == 0 and P in (1, 2, 4, 8) and P >= _radius(scheme)
-            and (n is None or n % W == 0))
+    return scheme != S.EULER and W % 32 == 0 and P in (1, 2, 4, 8) and (n is None or n % W == 0)
 
 
 def tune_single(scheme, dtype, n, probe_steps=None, cache=DEFAULT_CACHE, refresh=False, reps=2, threads=THREADS,

@@ -375,7 +375,7 @@ swept_status swept_init(const swept_config* cfg, swept_handle** out) {
   }
   if (cfg->warp_tiles == 1) {
     const int P = W / 32;
-    if (!h->tiled || g.X != 0 || im->C != 1 || W % 32 != 0 || (P != 1 && P != 2 && P != 4 && P != 8) || P < R ||
+    if (!h->tiled || g.X != 0 || im->C != 1 || W % 32 != 0 || (P != 1 && P != 2 && P != 4 && P != 8) ||
         g.chunk != 1 || (cfg->threads != 0 && cfg->threads != 32)) {
       delete h;
       return SWEPT_EINVAL;

@@ -17,8 +17,8 @@ struct Launch {
     return kk;
   }
   static int64_t smem_values(int M) { return swept_smem_values<Op>(M); }
-  // register tiers exist for scalar schemes with at least R points per lane
-  static constexpr bool p_ok(int P) { return P == 0 || (Op::C == 1 && P >= Op::R); }
+  // register tiers exist for scalar schemes
+  static constexpr bool p_ok(int P) { return P == 0 || Op::C == 1; }
   // fn(std::integral_constant<int, P>) for the kernel variant of g.P
   template <class Fn>
   static cudaError_t with_p(int P, Fn&& fn) {

@@ -407,7 +407,7 @@ struct RegCtx : Base {
   using T = typename Base::value_type;
   using Op = typename Base::op_type;
   static constexpr int R = Op::R;
-  static_assert(Op::C == 1 && P >= R, "register tiers need a scalar scheme and at least R points per lane");
+  static_assert(Op::C == 1 && P >= 1, "register tiers need a scalar scheme");
   T a[P], b[P];            // rows 0 (even tiers) and 1 (odd tiers)
   T ha[2 * R], hb[2 * R];  // halo of rows 0 / 1: [0, R) -> points 0..R-1, [R, 2R) -> points W+R..W+2R-1
   bool in_regs;
@@ -467,10 +467,24 @@ struct RegCtx : Base {
     T w[P + 2 * R];  // points p0 - R .. p0 + P + R - 1 of the source tier
 #pragma unroll
     for (int d = 0; d < R; ++d) {
-      const T x = __shfl_up_sync(0xffffffffu, src[P - R + d], 1);
-      w[d] = ln == 0 ? hs[d] : x;
-      const T y = __shfl_down_sync(0xffffffffu, src[d], 1);
-      w[R + P + d] = ln == 31 ? hs[R + d] : y;
+      // left halo point d is window point ln P + d: element el of lane ln - kl, or, for the
+      // first kl lanes, the window's own halo hs[ln P + d] (kl = 1 when P >= R)
+      const int kl = (R - d + P - 1) / P, el = d - R + kl * P;
+      const T x = __shfl_up_sync(0xffffffffu, src[el], kl);
+      T hx = hs[d];
+#pragma unroll
+      for (int m = 1; m < kl; ++m)
+        if (ln == m) hx = hs[m * P + d];
+      w[d] = ln < kl ? hx : x;
+      // right halo point d is window point R + (ln + 1) P + d: element er of lane ln + kr, or,
+      // for the last kr lanes, hs[R + d - m P] on lane 31 - m (kr = 1 when P >= R)
+      const int kr = 1 + d / P, er = d - (kr - 1) * P;
+      const T y = __shfl_down_sync(0xffffffffu, src[er], kr);
+      T hy = hs[R + d];
+#pragma unroll
+      for (int m = 1; m < kr; ++m)
+        if (ln == 31 - m) hy = hs[R + d - m * P];
+      w[R + P + d] = ln > 31 - kr ? hy : y;
     }
 #pragma unroll
     for (int i = 0; i < P; ++i) w[R + i] = src[i];

@@ -53,7 +53,7 @@ def cfg(S, scheme=None, **kw):
     dict(n=0), dict(n=-5), dict(dx=0.0), dict(dt=-1.0), dict(tile_w=12), dict(tile_w=4096),
     dict(tile_w=1000), dict(threads=48), dict(threads=2048), dict(dtype=7), dict(scheme=9),
     dict(bc=1),  # KS is periodic only
-    dict(warp_tiles=2), dict(warp_tiles=1, tile_w=32),  # KS needs at least 2 points per lane
+    dict(warp_tiles=2),
     dict(warp_tiles=1, tile_w=96), dict(warp_tiles=1, tile_w=512),  # W / 32 must be 1, 2, 4 or 8
     dict(warp_tiles=1, tile_w=64, threads=64), dict(warp_tiles=1, tile_w=64, chunk=3),
     dict(warp_tiles=1, scheme=2, tile_w=64, param0=1.4, bc=1),  # Euler keeps its tiers in shared memory

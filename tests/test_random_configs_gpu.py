@@ -47,7 +47,7 @@ def draw(rnd, S):
     W = 4 * R * rnd.choice([2, 4, 8, 16, 32, 64])
     mode = rnd.choice(["pass", "pass", "persistent", "cluster", "warp"])
     if mode == "warp":
-        P = rnd.choice([p for p in (1, 2, 4, 8) if p >= R])
+        P = rnd.choice([1, 2, 4, 8])
         W = 32 * P
         if scheme == "euler":
             mode = "pass"

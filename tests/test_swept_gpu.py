@@ -395,6 +395,13 @@ WARP_CASES = [
     ("ks", np.float32, 12 * 64, 64, 77, 0, 1),
     ("ks", np.float64, 16 * 128, 128, 555, 0, 2),
     ("ks", np.float64, 2 * 64, 64, 7, 0, 0),       # two tiles, remainder only
+    # KS with P = 1 < r: the 32-point register node (8 sub-steps = 4 timesteps a pass), halo
+    # points from lanes two away and from the window's halo at both warp ends
+    ("ks", np.float64, 64 * 32, 32, 1003, 0, 0),
+    ("ks", np.float32, 2 * 32, 32, 301, 0, 0),
+    ("ks", np.float64, 128 * 32, 32, 777, 0, 1),
+    ("ks", np.float32, 9 * 32, 32, 203, 0, 2),
+    ("ks", np.float64, 3 * 32, 32, 3, 0, 0),       # remainder only
 ]
 
 
