@@ -9,6 +9,11 @@
   python -m paper_1612_02495_gb300.run_case --scheme ks --slab 2 --n 1048576 --nsteps 1000 --tile 1024
       (the grid split over --slab ranks, all in this process on one GPU: every rank's launch i, then
       the transfers after it as device copies; checks the gathered result against swept_step_n)
+  python -m torch.distributed.run --nproc-per-node 8 --master-addr 127.0.0.1 -m paper_1612_02495_gb300.run_case \
+      --scheme ks --slab-dist 1 --grid 8388608 --nsteps 2000 --tile 1024
+      (one rank per process: rank r runs its slab on GPU LOCAL_RANK and trades edges over NCCL; with
+      --slab-host 1 every rank uses GPU 0 and the messages go through host memory over gloo; rank 0
+      gathers the grid and checks it against a whole-grid swept_step_n on its GPU)
 
 Used to profile a single kernel on a chosen size (e.g. under ncu).  One
 untimed warm-up solve precedes the timed repeats.
@@ -24,7 +29,8 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--scheme", default="ks", choices=["heat", "ks", "euler", "heat2d", "batch"])
     ap.add_argument("--dtype", default="f64", choices=["f32", "f64"])
-    ap.add_argument("--n", type=int, default=1 << 20)
+    # --grid is the same option, for launchers whose own options --n would abbreviate (torch.distributed.run)
+    ap.add_argument("--n", "--grid", dest="n", type=int, default=1 << 20)
     ap.add_argument("--nsteps", type=int, default=600)
     ap.add_argument("--path", default="swept", choices=["swept", "classic"])
     ap.add_argument("--tile", type=int, default=0)
@@ -37,6 +43,9 @@ def main(argv=None):
     ap.add_argument("--count", type=int, default=4096, help="batch: number of problems")
     ap.add_argument("--adjoint", type=int, default=0, help="heat / KS FP64: time the adjoint sweep")
     ap.add_argument("--slab", type=int, default=0, help="split the grid over this many ranks (one process)")
+    ap.add_argument("--slab-dist", type=int, default=0, help="split the grid over the torch.distributed ranks")
+    ap.add_argument("--slab-host", type=int, default=0,
+                    help="with --slab-dist: all ranks on GPU 0, messages staged through host memory over gloo")
     a = ap.parse_args(argv)
 
     import torch
@@ -64,6 +73,8 @@ def main(argv=None):
         p = inputs.euler_problem(n=a.n, dtype=npd)
         args = (S.EULER, dt_code, a.n, p["dx"], p["dt"], p["gamma"], S.BC_REFLECTIVE)
         u0 = p["U0"]
+    if a.slab_dist:
+        return run_slab_dist(a, S, torch, args, u0)
     if a.slab:
         return run_slab(a, S, torch, args, u0)
     sol = S.Solver(*args, tile_w=a.tile, threads=a.threads, chunk=a.chunk, persistent=a.persistent,
@@ -123,6 +134,62 @@ def run_slab(a, S, torch, args, u0):
         s.close()
     sol.close()
     return 0 if same else 1
+
+
+def run_slab_dist(a, S, torch, args, u0):
+    """The grid split over the ranks of a torch.distributed job, one slab per process."""
+    import os
+
+    import torch.distributed as dist
+
+    rank, world = int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(0 if a.slab_host else local)
+    dist.init_process_group("gloo" if a.slab_host else "nccl", rank=rank, world_size=world)
+    scheme, dt_code, n, dx, dt, p0, bc = args
+    slab = S.Slab(scheme, dt_code, n, dx, dt, p0, rank, world, bc=bc, tile_w=a.tile, threads=a.threads,
+                  chunk=a.chunk, warp_tiles=a.warp_tiles)
+    ug = torch.from_numpy(np.ascontiguousarray(u0))
+    u = slab.local_state(ug)
+    init = u.clone()
+    transport = S.dist_transport(stage_on_host=bool(a.slab_host))
+    slab.step(u, a.nsteps, transport)  # warm-up
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(a.repeat):
+        u.copy_(init)
+        dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        slab.step(u, a.nsteps, transport)
+        e1.record()
+        torch.cuda.synchronize()
+        dist.barrier()
+        times.append(e0.elapsed_time(e1))
+    t = torch.tensor([float(np.median(times))], dtype=torch.float64, device="cpu" if a.slab_host else "cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)  # the slowest rank
+    owned = slab.owned(u).cpu()
+    parts = [None] * world
+    dist.all_gather_object(parts, (slab.layout["x0"], owned.numpy()))
+    same = None
+    if rank == 0:
+        got = np.concatenate([p[1] for p in sorted(parts, key=lambda q: q[0])], axis=1).reshape(-1)
+        sol = S.Solver(scheme, dt_code, n, dx, dt, p0, bc, tile_w=a.tile, threads=a.threads, chunk=a.chunk,
+                       warp_tiles=a.warp_tiles)
+        w = ug.cuda()
+        sol.step(w, a.nsteps)
+        torch.cuda.synchronize()
+        same = bool(np.array_equal(got, w.reshape(-1).cpu().numpy()))
+        sol.close()
+        ms = float(t.item())
+        print(json.dumps({"scheme": a.scheme, "dtype": a.dtype, "n": n, "nsteps": a.nsteps, "ranks": world,
+                          "backend": "gloo, host-staged, one GPU" if a.slab_host else "nccl, one GPU a rank",
+                          "ms": ms, "cell_updates_per_s": n * a.nsteps / (ms * 1e-3),
+                          "launches_per_rank": slab.launch_count(a.nsteps), "equal_to_whole_grid": same}))
+    slab.close()
+    dist.destroy_process_group()
+    return 0 if (rank != 0 or same) else 1
 
 
 def run_heat2d(a, S, inputs, torch, npd, dt_code):
