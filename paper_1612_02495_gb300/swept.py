@@ -733,19 +733,25 @@ class SlabSym:
         if st != SWEPT_OK:
             raise SweptError(st, "swept_slab_sym_init rejected the configuration")
         self.h = h.value
+        self._ph = None
         self.nsteps = int(nsteps)
-        # the launch count and transfer lists come from a slab handle of the same configuration
-        ph = _H()
-        check(swept_slab_init(ctypes.byref(cfg), int(rank), int(nranks), ctypes.byref(ph)), None, "swept_slab_init")
-        self._ph = ph.value
-        self._views = []
-        for region in range(3):
-            p = ctypes.POINTER(_I64)()
-            nv = _I64()
-            check(swept_slab_sym_buffer(self.h, region, ctypes.byref(p), ctypes.byref(nv)), None,
-                  "swept_slab_sym_buffer")
-            a = np.ctypeslib.as_array(p, shape=(int(nv.value), 2)) if nv.value else np.zeros((0, 2), np.int64)
-            self._views.append(torch.from_numpy(a))
+        try:
+            # the launch count and transfer lists come from a slab handle of the same configuration
+            ph = _H()
+            check(swept_slab_init(ctypes.byref(cfg), int(rank), int(nranks), ctypes.byref(ph)), None,
+                  "swept_slab_init")
+            self._ph = ph.value
+            self._views = []
+            for region in range(3):
+                p = ctypes.POINTER(_I64)()
+                nv = _I64()
+                check(swept_slab_sym_buffer(self.h, region, ctypes.byref(p), ctypes.byref(nv)), None,
+                      "swept_slab_sym_buffer")
+                a = np.ctypeslib.as_array(p, shape=(int(nv.value), 2)) if nv.value else np.zeros((0, 2), np.int64)
+                self._views.append(torch.from_numpy(a))
+        except Exception:
+            self.close()
+            raise
         self.n = int(n)
 
     def launch_count(self, nsteps):
