@@ -550,7 +550,7 @@ swept_status swept_slab_check(const swept_config* cfg, int32_t nranks, int64_t n
       }
     }
     for (int k = 0; k < nranks; ++k) {
-      Xfer x[8];
+      Xfer x[kMaxXfers];
       const int m = slab_xfers(g, r[(size_t)k]->sl, n_sub, i, x);
       xs[(size_t)k].assign(x, x + m);
     }

@@ -174,7 +174,7 @@ swept_status swept_slab_launch(swept_slab* h, void* u_dev, int64_t nsteps, int64
 swept_status swept_slab_xfers(const swept_slab* h, int64_t nsteps, int64_t i, swept_slab_xfer* out, int32_t cap,
                               int32_t* n) {
   if (!h || !n || nsteps < 0 || cap < 0 || (cap > 0 && !out)) return SWEPT_EINVAL;
-  swept::Xfer x[8];
+  swept::Xfer x[swept::kMaxXfers];
   const int m = swept::slab_xfers(h->g, h->sl, nsteps * h->g.S, i, x);
   if (m > cap) return SWEPT_EINVAL;
   for (int j = 0; j < m; ++j) {

@@ -71,6 +71,10 @@ inline LaunchDesc launch_at(const Geom& g, int64_t n_sub, int64_t i) {
   return d;
 }
 
+// at most this many transfers follow one launch: a state message per component (C <= 3) each
+// way, then one edge message each way
+constexpr int kMaxXfers = 2 * 3 + 2;
+
 // one transfer between neighbouring ranks (the C ABI's swept_slab_xfer)
 struct Xfer {
   int peer;    // -1 left neighbour, +1 right neighbour
@@ -94,7 +98,7 @@ inline Slab make_slab(const Geom& g, int rank, int nranks) {
 }
 
 // The transfers due after launch i of an n_sub-sub-timestep solve (before
-// launch i + 1), in the order a rank posts them; returns how many (<= 2 C + 2).
+// launch i + 1), in the order a rank posts them; returns how many (<= 2 C + 2 <= kMaxXfers).
 // A rank's k-th send to a neighbour matches that neighbour's k-th receive from
 // the opposite side.
 inline int slab_xfers(const Geom& g, const Slab& sl, int64_t n_sub, int64_t i, Xfer* out) {
