@@ -100,3 +100,43 @@ def test_random_configuration(S, case):
     got = u.cpu().numpy()
     assert np.array_equal(got, v.cpu().numpy()), "swept != classic"
     assert np.array_equal(got, ref), "swept != oracle"
+
+
+# --- the 2D decomposition ---------------------------------------------------------------------
+
+def draw2d(rnd):
+    dtype = rnd.choice([np.float64, np.float32])
+    W = rnd.choice([8, 12, 16, 20, 24, 32, 48, 64] + ([96, 128] if dtype == np.float32 else []))
+    nx, ny = W * rnd.randint(2, 9), W * rnd.randint(2, 9)
+    threads = rnd.choice([32, 64, 128, 256, 512, 1024])
+    return dict(dtype=dtype, W=W, nx=nx, ny=ny, threads=threads, bc=rnd.choice([0, 1]),
+                persistent=rnd.choice([0, 1]), nsteps=rnd.randint(1, 3 * W))
+
+
+CASES2D = [draw2d(random.Random(20161209 + i)) for i in range(30)]
+
+
+@pytest.mark.parametrize("case", CASES2D, ids=["%s-%dx%d-W%d-t%d-bc%d-p%d-s%d" % (
+    "f64" if c["dtype"] == np.float64 else "f32", c["nx"], c["ny"], c["W"], c["threads"], c["bc"], c["persistent"],
+    c["nsteps"]) for c in CASES2D])
+def test_random_configuration_2d(S, case):
+    import torch
+
+    c = case
+    code = S.F64 if c["dtype"] == np.float64 else S.F32
+    q = inputs.heat2d_problem(nx=c["nx"], ny=c["ny"], dtype=c["dtype"])
+    sol = S.Solver2D(code, c["nx"], c["ny"], q["dx"], q["dt"], q["alpha"], tile_w=c["W"], threads=c["threads"],
+                     bc=c["bc"], persistent=c["persistent"])
+    u = torch.from_numpy(q["u0"]).cuda()
+    v = u.clone()
+    sol.step(u, c["nsteps"])
+    sol.classic(v, c["nsteps"])
+    torch.cuda.synchronize()
+    sol.sync_status()
+    sol.close()
+    if S.DEBUG_BUILD:
+        enabled, rec = S.debug_status()
+        assert enabled and rec is None, rec
+    ref = oracle.heat2d(q["u0"], q["dx"], q["dt"], q["alpha"], c["nsteps"], bc=c["bc"], threads=THREADS)
+    assert np.array_equal(u.cpu().numpy(), v.cpu().numpy()), "2D swept != classic"
+    assert np.array_equal(u.cpu().numpy(), ref), "2D swept != oracle"
