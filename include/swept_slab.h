@@ -112,7 +112,8 @@ void swept_slab_free(swept_slab* h);
  * that every (point, sub-timestep) is computed exactly once over all ranks, and
  * that each rank ends holding sub-timestep n_sub on [x0, x1).  *computed gets
  * the number of point-updates.  On failure returns SWEPT_EDEVICE with the
- * first violation in msg.  Limited to (nsteps S + 1) n <= 4e8. */
+ * first violation in msg.  Limited to (nsteps S + 1) n <= 4e8 and
+ * (nsteps S + 1) n nranks <= 2e9. */
 swept_status swept_slab_check(const swept_config* cfg, int32_t nranks, int64_t nsteps, int64_t* computed, char* msg,
                               size_t len);
 

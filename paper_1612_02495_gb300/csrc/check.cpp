@@ -525,6 +525,14 @@ swept_status swept_slab_check(const swept_config* cfg, int32_t nranks, int64_t n
                               size_t len) {
   using namespace swept;
   if (!cfg || nranks < 1 || nsteps < 0) return SWEPT_EINVAL;
+  {
+    // every rank's replay keeps a count per (sub-timestep, point) of the whole grid
+    const int stages = cfg->scheme == SWEPT_HEAT ? 1 : 2;
+    if ((double)(nsteps * stages + 1) * (double)cfg->n * (double)nranks > 2e9) {
+      set_msg(msg, len, "slab check too large ((nsteps S + 1) n nranks > 2e9)");
+      return SWEPT_EINVAL;
+    }
+  }
   std::vector<swept_slab_sym*> r((size_t)nranks, nullptr);
   auto cleanup = [&]() {
     for (auto* p : r) swept_slab_sym_free(p);

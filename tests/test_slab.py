@@ -292,3 +292,9 @@ def test_slab_calls_validate_before_touching_a_device(S):
         assert S.swept_slab_launch(h, fake, 10, 0, None) == S.SWEPT_ECUDA
     S.swept_slab_free(h)
     S.swept_slab_free(None)
+
+
+def test_slab_check_refuses_oversized_replays(S):
+    with pytest.raises(S.SweptError) as e:
+        S.slab_check(S.HEAT, S.F64, 1 << 20, 0.1, 1e-3, 1.0, 64, 100, tile_w=1024)  # 101 x 2^20 x 64 > 2e9
+    assert e.value.status == S.SWEPT_EINVAL
